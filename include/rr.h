@@ -1,0 +1,252 @@
+/*
+ * rr.h - C ABI of the GB300 ray-reordering library (librr.so).
+ *
+ * The library implements, per bounce of a wavefront ray tracer, the pipeline
+ * studied by Meister, Boksansky, Guthe and Bittner, "On Ray Reordering
+ * Techniques for Faster GPU Ray Tracing" (I3D 2020):
+ *
+ *   rr_compute_keys  per-ray sorting key (Section 3.1, Figure 2)
+ *   rr_sort          stable LSD radix sort of (key, ray index) pairs (Section 3.2)
+ *   rr_permute       the extra pass that moves ray data into sorted order (Section 3.2)
+ *   rr_trace         closest-hit traversal of a BVH; it does not depend on the order
+ *                    of the rays (Section 1: reordering is agnostic to the trace kernel)
+ *   rr_length_table_accumulate
+ *                    the adaptive ray-length cache updated after each trace (Section 3.1.6)
+ *
+ * Conventions shared by every call:
+ *  - Device buffers are owned by the caller.  The library owns only the opaque
+ *    handles (rr_bvh, rr_length_table, rr_pipeline) and the device memory behind them.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy default
+ *    stream) and the call returns without synchronising, unless stated otherwise.
+ *  - Arguments are checked on the host before anything is enqueued.  A bad
+ *    argument returns RR_ERR_INVALID_ARG and enqueues nothing.  n == 0 is a
+ *    no-op that returns RR_OK.
+ *  - Failures inside kernels (a radix-sort look-back that waited too long, a
+ *    traversal stack overflow) never trap: the kernel records a flag in a
+ *    per-device error word and finishes.  rr_device_error() reads and clears it.
+ *  - Ray layout (structure of arrays, 16-byte aligned):
+ *      o_tmin  float4 per ray: origin.x, origin.y, origin.z, tmin
+ *      d_tmax  float4 per ray: direction.x, .y, .z, tmax
+ *      payload uint32 per ray: caller data moved with the ray (optional)
+ *  - Hit layout: float4 per ray: t, u, v, triangle id (the id's uint32 bits).
+ *    A miss is t = +inf, u = v = 0, id = 0xFFFFFFFF.  Hits are written in the
+ *    order of the rays that were traced.
+ *  - Keys are uint32 when bits <= 32 and uint64 when 32 < bits <= 64.
+ */
+#ifndef RR_H
+#define RR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RR_OK = 0,
+    RR_ERR_INVALID_ARG = 1, /* a pointer, size or option failed the host-side checks */
+    RR_ERR_CUDA = 2,        /* a CUDA runtime call failed (see rr_last_error_message) */
+    RR_ERR_OOM = 3,         /* a library-owned allocation failed */
+    RR_ERR_TIMEOUT = 4,     /* device: a bounded wait gave up (radix-sort look-back) */
+    RR_ERR_STACK = 5,       /* device: a traversal stack would have overflowed */
+    RR_ERR_UNSUPPORTED = 6  /* a valid request this build does not handle */
+} rr_status;
+
+/* Device error flags accumulated in the per-device error word. */
+#define RR_DEVERR_LOOKBACK_TIMEOUT 0x1u
+#define RR_DEVERR_TRACE_STACK 0x2u
+
+/* Sorting-key layouts (Section 3.1, Figure 2). */
+typedef enum {
+    RR_KEY_AILA = 0,         /* origin and direction interleaved; each quantised direction
+                                component has three leading zero bits (Section 3.1.4) */
+    RR_KEY_AILA_COMPACT = 1, /* the same bits with the leading zeros removed (Section 3.1.4) */
+    RR_KEY_TWO_POINT = 2     /* origin and estimated termination point interleaved,
+                                origin first in every level (Section 3.1.5) */
+} rr_key_layout;
+
+/* Termination estimate of the Two Point key (Section 3.1.6). */
+typedef enum {
+    RR_T_FIXED = 0,    /* ratio * largest extent of the scene box (paper: ratio 0.25) */
+    RR_T_ADAPTIVE = 1, /* mean ray length of the ray's cell in a rr_length_table */
+    RR_T_GIVEN = 2     /* caller-supplied lengths, e.g. real hits ("Two Point Real") */
+} rr_t_source;
+
+typedef struct rr_bvh rr_bvh;
+typedef struct rr_length_table rr_length_table;
+typedef struct rr_pipeline rr_pipeline;
+
+typedef struct {
+    uint32_t layout;   /* rr_key_layout */
+    uint32_t bits;     /* key length b, 1..64: the first b bits of the interleaved string */
+    uint32_t t_source; /* rr_t_source; read only for RR_KEY_TWO_POINT */
+    float ratio;       /* RR_T_FIXED: estimate = ratio * E */
+    float aabb_lo[3];  /* scene box: origins, directions and termination points are */
+    float aabb_hi[3];  /* quantised per axis inside it (finite, lo <= hi) */
+    const float *t_given;          /* RR_T_GIVEN: device, n world-space lengths */
+    const rr_length_table *table;  /* RR_T_ADAPTIVE: a table created for the same box */
+} rr_key_params;
+
+typedef struct {
+    uint32_t n_tris;
+    uint32_t n_nodes;  /* 8-wide nodes */
+    uint32_t n_leaves; /* leaf slots (1..4 triangles each) */
+    uint32_t depth;    /* node levels from the root to the deepest node */
+    uint64_t node_bytes;
+    uint64_t tri_bytes;
+    float aabb_lo[3];
+    float aabb_hi[3];
+    double build_seconds;
+} rr_bvh_info;
+
+/* ---------------------------------------------------------------- keys */
+
+/*
+ * rr_compute_keys - one sorting key per ray (Section 3.1; layouts in Figure 2).
+ *
+ * Each coordinate is mapped per axis into [0,1] by the scene box (params->aabb),
+ * clamped, and quantised to 32 bits by truncation.  Directions are normalised
+ * and mapped from [-1,1] to [0,1].  The Aila layouts interleave origin and
+ * direction (the direction shifted right by 3: its three leading zero bits);
+ * the compact layout drops the nine zero bits.  The Two Point layout
+ * interleaves the origin with p = o + t_est * normalize(d), where t_est comes
+ * from params->t_source; a non-finite t_est is replaced by 4 * E.  The key is
+ * the first `bits` bits of the 192-bit interleaved string, x before y before z.
+ * All float arithmetic is correctly rounded binary32, so keys are exact.
+ *
+ * o_tmin, d_tmax: device, n float4 each.  keys_out: device, n uint32 (bits <= 32)
+ * or n uint64.  For RR_T_ADAPTIVE the table must have been created for the same
+ * box as params->aabb.
+ */
+rr_status rr_compute_keys(const float *o_tmin, const float *d_tmax, uint32_t n,
+                          const rr_key_params *params, void *keys_out, void *stream);
+
+/* ---------------------------------------------------------------- sort */
+
+/*
+ * rr_sort_workspace_size - device workspace bytes rr_sort needs for n keys of
+ * `bits` bits sorted with `radix_bits`-bit digits (4 or 8).
+ */
+rr_status rr_sort_workspace_size(uint32_t n, uint32_t bits, uint32_t radix_bits, size_t *bytes);
+
+/*
+ * rr_sort - stable least-significant-digit radix sort of (key, index) pairs
+ * (Section 3.2: "the sorting is performed on key-index pairs first").
+ *
+ * perm_out[i] = index of the i-th smallest key; equal keys keep their input
+ * order.  keys_in (device, uint32 for bits <= 32 else uint64) is not modified;
+ * only bits [0, bits) are sorted and the higher bits must be zero.  keys_out
+ * (device, same type, may be NULL) receives the sorted keys.  keys_in, keys_out
+ * and perm_out must not overlap.  workspace: device, at least
+ * rr_sort_workspace_size() bytes, 256-byte aligned, owned by the caller and
+ * free again once the work on `stream` has completed.  n < 2^30.
+ * One histogram pass plus ceil(bits / radix_bits) onesweep passes are enqueued.
+ */
+rr_status rr_sort(const void *keys_in, void *keys_out, uint32_t *perm_out, uint32_t n,
+                  uint32_t bits, uint32_t radix_bits, void *workspace, size_t workspace_bytes,
+                  void *stream);
+
+/* ---------------------------------------------------------------- reorder */
+
+/*
+ * rr_permute - the reorder pass of Section 3.2: out[i] = in[perm[i]] for
+ * o_tmin, d_tmax and (when both pointers are non-NULL) payload.  Bitwise copy.
+ * perm: device, n indices < n.  Inputs and outputs must not overlap.
+ */
+rr_status rr_permute(const float *o_tmin_in, const float *d_tmax_in, const uint32_t *payload_in,
+                     const uint32_t *perm, uint32_t n, float *o_tmin_out, float *d_tmax_out,
+                     uint32_t *payload_out, void *stream);
+
+/* ---------------------------------------------------------------- BVH and trace */
+
+/*
+ * rr_build_bvh - builds, on the host, a BVH with 8-wide compressed nodes over
+ * a triangle soup (tris_host: 9 floats per triangle, v0 v1 v2) and uploads it
+ * to the current device.  Synchronous.  The paper's trace is RTX hardware; this
+ * BVH serves the software trace kernel.  The handle owns its device memory.
+ */
+rr_status rr_build_bvh(const float *tris_host, uint32_t n_tris, rr_bvh **out);
+rr_status rr_bvh_destroy(rr_bvh *bvh);
+rr_status rr_bvh_get_info(const rr_bvh *bvh, rr_bvh_info *info);
+
+/*
+ * rr_trace - closest hit of every ray: the smallest t with tmin < t < tmax over
+ * all triangles (two-sided), with its barycentrics and triangle id (index in the
+ * soup given to rr_build_bvh).  o_tmin, d_tmax: device, n float4.  hits_out:
+ * device, n float4.  The kernel is persistent: warps take batches of 32
+ * consecutive rays from a queue, so the order of the rays decides which rays
+ * share a warp (the effect reordering is meant to improve, Section 4.2).
+ */
+rr_status rr_trace(const rr_bvh *bvh, const float *o_tmin, const float *d_tmax, uint32_t n,
+                   float *hits_out, void *stream);
+
+/* ---------------------------------------------------------------- ray-length table */
+
+/*
+ * Adaptive termination estimate (Section 3.1.6): a table of 2^20 cells indexed
+ * by the 20-bit compacted Aila code of (origin, direction).  Each cell holds
+ * the sum of ray lengths (uint64, fixed point in units of E / 2^24) and the
+ * number of rays (uint32).  Every cell starts with one dummy ray of length
+ * 0.25 * E, E = largest extent of the box.  Lengths are t * |d| of rays that
+ * hit, clamped to [0, 64 * E].  Integer accumulation makes the table
+ * independent of the order of the rays.
+ */
+rr_status rr_length_table_create(const float aabb_lo[3], const float aabb_hi[3],
+                                 rr_length_table **out, void *stream);
+rr_status rr_length_table_reset(rr_length_table *table, void *stream);
+rr_status rr_length_table_accumulate(rr_length_table *table, const float *o_tmin,
+                                     const float *d_tmax, const float *hits, uint32_t n,
+                                     void *stream);
+/* Copies the cells to host arrays of 2^20 entries each (synchronous). */
+rr_status rr_length_table_read(const rr_length_table *table, uint64_t *sum_host,
+                               uint32_t *cnt_host);
+/* Overwrites the cells from host arrays of 2^20 entries each (synchronous). */
+rr_status rr_length_table_write(rr_length_table *table, const uint64_t *sum_host,
+                                const uint32_t *cnt_host);
+rr_status rr_length_table_destroy(rr_length_table *table);
+
+/* ---------------------------------------------------------------- one bounce */
+
+/*
+ * rr_pipeline - one bounce of the reordered path: keys -> sort -> permute ->
+ * trace (-> length-table update when the key uses RR_T_ADAPTIVE).  The handle
+ * owns the workspace and the sorted ray buffers for up to max_n rays.
+ * key params are copied; their pointers (t_given, table) must stay valid.
+ */
+rr_status rr_pipeline_create(const rr_bvh *bvh, uint32_t max_n, const rr_key_params *params,
+                             uint32_t radix_bits, rr_pipeline **out);
+rr_status rr_pipeline_destroy(rr_pipeline *p);
+
+/*
+ * rr_pipeline_run - device buffers.  Writes hits_out (device, n float4) and,
+ * when payload_in/payload_out are non-NULL, the payloads, both in sorted order.
+ */
+rr_status rr_pipeline_run(rr_pipeline *p, const float *o_tmin, const float *d_tmax,
+                          const uint32_t *payload_in, uint32_t n, float *hits_out,
+                          uint32_t *payload_out, void *stream);
+
+/*
+ * rr_pipeline_run_host - host buffers (pinned for full copy speed): copies the
+ * rays to the device, runs the bounce, copies hits and payloads back, and
+ * synchronises `stream` before returning.
+ */
+rr_status rr_pipeline_run_host(rr_pipeline *p, const float *o_tmin_host, const float *d_tmax_host,
+                               const uint32_t *payload_host, uint32_t n, float *hits_host,
+                               uint32_t *payload_out_host, void *stream);
+
+/* ---------------------------------------------------------------- diagnostics */
+
+/* Reads and clears the current device's error word (RR_DEVERR_* flags); synchronising. */
+rr_status rr_device_error(uint32_t *flags_out);
+const char *rr_status_string(rr_status s);
+/* Message of the last failing call on this thread ("" if none). */
+const char *rr_last_error_message(void);
+/* Number of kernels the library has launched in this process (all devices). */
+uint64_t rr_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RR_H */

@@ -1,0 +1,104 @@
+// Internal definitions shared by the translation units of librr.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+#include "../../include/rr.h"
+
+namespace rr {
+
+constexpr uint32_t kMiss = 0xFFFFFFFFu;
+constexpr uint32_t kTableCells = 1u << 20;
+
+// ------------------------------------------------------------------ host helpers
+
+// Records `msg` as this thread's last error message and returns `s`.
+rr_status fail(rr_status s, const std::string &msg);
+rr_status fail_cuda(cudaError_t e, const char *what);
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Per-device state: the error word and cached properties.
+struct DeviceState {
+    uint32_t *err = nullptr;      // device word with RR_DEVERR_* flags
+    uint32_t *counters = nullptr;  // pool of trace work-queue counters (zero at rest)
+    int sm_count = 0;
+    int max_smem_optin = 0;
+    std::atomic<uint32_t> next_counter{0};
+};
+constexpr uint32_t kCounterPool = 4096;
+
+// Returns the state of the current device (initialised on first use) or null.
+DeviceState *device_state(rr_status *st);
+
+// Counts kernel launches made by the library.
+void note_launches(uint32_t k);
+
+// A kernel launch check: returns RR_OK or RR_ERR_CUDA with the message recorded.
+rr_status check_launch(const char *what);
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+inline bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+inline bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
+    uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+
+// ------------------------------------------------------------------ library-owned objects
+
+struct Box {
+    float lo[3];
+    float hi[3];
+};
+
+}  // namespace rr
+
+struct rr_length_table {
+    int device;
+    rr::Box box;
+    float E;                 // largest extent of box
+    unsigned long long *cells;  // 2^20 x {sum (u64), count (u64 slot, low 32 bits used)}
+};
+
+// Compressed 8-wide BVH node (80 bytes, five 16-byte loads).
+//   A child box is p + q * 2^(e - 127) per axis: q in [qlo, qhi] (8 bits each).
+//   meta[slot]: 0 = empty; bit 7 set = inner child, node index child_base + (meta & 7);
+//   otherwise a leaf of ((meta >> 5) & 3) + 1 triangles starting at
+//   tri_base + (meta & 31) in the BVH-ordered triangle array.
+struct alignas(16) RRNode8 {
+    float px, py, pz;
+    uint8_t ex, ey, ez, pad0;
+    uint32_t child_base;
+    uint32_t tri_base;
+    uint8_t meta[8];
+    uint8_t qlo_x[8];
+    uint8_t qlo_y[8];
+    uint8_t qlo_z[8];
+    uint8_t qhi_x[8];
+    uint8_t qhi_y[8];
+    uint8_t qhi_z[8];
+};
+static_assert(sizeof(RRNode8) == 80, "node layout");
+
+// Triangle in BVH order: v0, e1 = v1 - v0, e2 = v2 - v0; w of the first float4
+// holds the original triangle id.
+struct alignas(16) RRTri {
+    float4 v0_id;
+    float4 e1;
+    float4 e2;
+};
+
+struct rr_bvh {
+    int device;
+    RRNode8 *nodes;   // device
+    RRTri *tris;      // device
+    uint32_t n_nodes;
+    uint32_t n_tris;
+    uint32_t root_is_leaf;  // scenes of 1..4 triangles: no inner node, the root is one leaf
+    uint32_t root_leaf_ref;
+    rr_bvh_info info;
+};

@@ -1,0 +1,108 @@
+// Device arithmetic of the sorting keys (Section 3.1, Figure 2).
+//
+// Every float operation is a correctly rounded binary32 intrinsic, so that the
+// integer results (quantised coordinates, table cells, fixed-point lengths)
+// do not depend on instruction selection (no multiply-add contraction).
+#pragma once
+
+#include <stdint.h>
+
+namespace rr {
+
+// x in [0,1] -> 32-bit cell by truncation; >= 1 -> all ones; <= 0 or NaN -> 0.
+__device__ __forceinline__ uint32_t quantise_unit(float x) {
+    if (!(x > 0.0f)) return 0u;
+    if (x >= 1.0f) return 0xFFFFFFFFu;
+    return __float2uint_rz(__fmul_rn(x, 4294967296.0f));  // times 2^32 is exact
+}
+
+struct QuantFrame {
+    float lo[3];
+    float inv[3];  // 1 / extent, or 0 for a flat axis
+    float E;       // largest extent
+};
+
+__device__ __forceinline__ QuantFrame make_frame(const float lo[3], const float hi[3]) {
+    QuantFrame f;
+    float e = 0.0f;
+    for (int c = 0; c < 3; ++c) {
+        float ext = __fsub_rn(hi[c], lo[c]);
+        f.lo[c] = lo[c];
+        f.inv[c] = ext > 0.0f ? __fdiv_rn(1.0f, ext) : 0.0f;
+        if (c == 0 || ext > e) e = ext;
+    }
+    f.E = e;
+    return f;
+}
+
+__device__ __forceinline__ uint32_t quantise_coord(const QuantFrame &f, int c, float p) {
+    return quantise_unit(__fmul_rn(__fsub_rn(p, f.lo[c]), f.inv[c]));
+}
+
+// |d| with the squares summed left to right.
+__device__ __forceinline__ float length3(float x, float y, float z) {
+    float s = __fmul_rn(x, x);
+    s = __fadd_rn(s, __fmul_rn(y, y));
+    s = __fadd_rn(s, __fmul_rn(z, z));
+    return __fsqrt_rn(s);
+}
+
+// Spreads the low 11 bits of x so that bit i lands on bit 6i.
+__device__ __forceinline__ uint64_t spread6(uint64_t x) {
+    x &= 0x7FFull;
+    x = (x | (x << 40)) & 0x00070000000000FFull;
+    x = (x | (x << 20)) & 0x000700000F00000Full;
+    x = (x | (x << 10)) & 0x1003003003003003ull;
+    x = (x | (x << 5)) & 0x1041041041041041ull;
+    return x;
+}
+
+// Spreads the low 3 bits of x so that bit i lands on bit 3i.
+__device__ __forceinline__ uint32_t spread3_3(uint32_t x) {
+    return (x & 1u) | ((x & 2u) << 2) | ((x & 4u) << 4);
+}
+
+// First 64 bits of the string whose level L (from the top) holds bit 31-L of
+// c[0], c[1], ..., c[5] in that order (Aila with c[3..5] = q(d) >> 3, and Two
+// Point with c[3..5] = q(p)).
+__device__ __forceinline__ uint64_t interleave6_64(const uint32_t c[6]) {
+    uint64_t hi = 0;
+#pragma unroll
+    for (int s = 0; s < 6; ++s) hi |= spread6(c[s] >> 22) << (5 - s);  // levels 0..9
+    uint64_t tail = ((uint64_t)((c[0] >> 21) & 1u) << 3) | ((uint64_t)((c[1] >> 21) & 1u) << 2) |
+                    ((uint64_t)((c[2] >> 21) & 1u) << 1) | (uint64_t)((c[3] >> 21) & 1u);
+    return (hi << 4) | tail;  // level 10, first four slots
+}
+
+// The compact string: levels 0..2 carry only c[0..2] (the always-zero
+// direction slots of the Aila string are dropped), later levels all six.
+__device__ __forceinline__ uint64_t interleave_compact_64(const uint32_t c[6]) {
+    uint32_t head = (spread3_3(c[0] >> 29) << 2) | (spread3_3(c[1] >> 29) << 1) |
+                    spread3_3(c[2] >> 29);  // 9 bits, levels 0..2
+    uint64_t body = 0;
+#pragma unroll
+    for (int s = 0; s < 6; ++s) body |= spread6((c[s] >> 20) & 0x1FFu) << (5 - s);  // levels 3..11
+    return ((uint64_t)head << 55) | (body << 1) | (uint64_t)((c[0] >> 19) & 1u);  // + level 12, x
+}
+
+// Quantised origin and direction of a ray (direction normalised, mapped to [0,1]).
+__device__ __forceinline__ void quantise_ray(const QuantFrame &f, float4 o, float4 d, uint32_t qo[3],
+                                             uint32_t qd[3], float dh[3]) {
+    qo[0] = quantise_coord(f, 0, o.x);
+    qo[1] = quantise_coord(f, 1, o.y);
+    qo[2] = quantise_coord(f, 2, o.z);
+    float len = length3(d.x, d.y, d.z);
+    dh[0] = len > 0.0f ? __fdiv_rn(d.x, len) : 0.0f;
+    dh[1] = len > 0.0f ? __fdiv_rn(d.y, len) : 0.0f;
+    dh[2] = len > 0.0f ? __fdiv_rn(d.z, len) : 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) qd[c] = quantise_unit(__fmul_rn(__fadd_rn(dh[c], 1.0f), 0.5f));
+}
+
+// 20-bit compacted Aila code: the length-table cell (Section 3.1.6).
+__device__ __forceinline__ uint32_t table_cell(const uint32_t qo[3], const uint32_t qd[3]) {
+    uint32_t c[6] = {qo[0], qo[1], qo[2], qd[0] >> 3, qd[1] >> 3, qd[2] >> 3};
+    return (uint32_t)(interleave_compact_64(c) >> 44);
+}
+
+}  // namespace rr

@@ -1,0 +1,288 @@
+// Sorting keys (Section 3.1, Figure 2) and the adaptive ray-length table
+// (Section 3.1.6).
+#include <cmath>
+#include <cstring>
+
+#include "rr_common.cuh"
+#include "rr_keymath.cuh"
+
+namespace rr {
+
+struct KeyArgs {
+    const float4 *o_tmin;
+    const float4 *d_tmax;
+    uint32_t n;
+    uint32_t bits;
+    float lo[3], hi[3];
+    float ratio;
+    const float *t_given;
+    const ulonglong2 *table;  // cells {sum, count}
+    void *keys;
+};
+
+// One ray per thread: two 16-byte loads, quantisation, interleave, one store.
+template <int LAYOUT, int TSRC, typename KeyT>
+__global__ void __launch_bounds__(256) key_kernel(KeyArgs a) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const QuantFrame f = make_frame(a.lo, a.hi);
+    float4 o = __ldg(a.o_tmin + i);
+    float4 d = __ldg(a.d_tmax + i);
+    uint32_t qo[3], qd[3];
+    float dh[3];
+    quantise_ray(f, o, d, qo, qd, dh);
+    uint64_t key64;
+    if (LAYOUT == RR_KEY_TWO_POINT) {
+        float t;
+        if (TSRC == RR_T_FIXED) {
+            t = __fmul_rn(a.ratio, f.E);
+        } else if (TSRC == RR_T_GIVEN) {
+            t = __ldg(a.t_given + i);
+        } else {
+            // mean length of the ray's cell, in units of E / 2^24
+            ulonglong2 cell = __ldg(a.table + table_cell(qo, qd));
+            if (cell.y == 0ull) {
+                t = __fmul_rn(0.25f, f.E);
+            } else {
+                unsigned long long mean = cell.x / cell.y;
+                t = __fmul_rn(__fmul_rn(__ull2float_rn(mean), 5.9604644775390625e-8f), f.E);
+            }
+        }
+        if (!isfinite(t)) t = __fmul_rn(4.0f, f.E);
+        uint32_t c[6];
+        c[0] = qo[0];
+        c[1] = qo[1];
+        c[2] = qo[2];
+        c[3] = quantise_coord(f, 0, __fadd_rn(o.x, __fmul_rn(dh[0], t)));
+        c[4] = quantise_coord(f, 1, __fadd_rn(o.y, __fmul_rn(dh[1], t)));
+        c[5] = quantise_coord(f, 2, __fadd_rn(o.z, __fmul_rn(dh[2], t)));
+        key64 = interleave6_64(c);
+    } else {
+        uint32_t c[6] = {qo[0], qo[1], qo[2], qd[0] >> 3, qd[1] >> 3, qd[2] >> 3};
+        key64 = LAYOUT == RR_KEY_AILA ? interleave6_64(c) : interleave_compact_64(c);
+    }
+    uint64_t key = key64 >> (64 - a.bits);
+    static_cast<KeyT *>(a.keys)[i] = (KeyT)key;
+}
+
+template <int LAYOUT, int TSRC>
+static void launch_keys(const KeyArgs &a, bool wide, cudaStream_t s) {
+    dim3 grid((a.n + 255) / 256);
+    if (wide)
+        key_kernel<LAYOUT, TSRC, unsigned long long><<<grid, 256, 0, s>>>(a);
+    else
+        key_kernel<LAYOUT, TSRC, uint32_t><<<grid, 256, 0, s>>>(a);
+}
+
+__global__ void table_init_kernel(ulonglong2 *cells) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kTableCells) cells[i] = make_ulonglong2(4194304ull /* 0.25 * 2^24 */, 1ull);
+}
+
+// After a trace: rays that hit add their fixed-point length to their cell.
+// Lanes of a warp that share a cell combine first (match_any + warp reduce),
+// then one lane issues the two 64-bit atomics.
+__global__ void __launch_bounds__(256) table_accumulate_kernel(unsigned long long *cells, float lo0,
+                                                               float lo1, float lo2, float hi0, float hi1,
+                                                               float hi2, const float4 *o_tmin,
+                                                               const float4 *d_tmax, const float4 *hits,
+                                                               uint32_t n) {
+    const float lo[3] = {lo0, lo1, lo2}, hi[3] = {hi0, hi1, hi2};
+    const QuantFrame f = make_frame(lo, hi);
+    const float invE = __fdiv_rn(1.0f, f.E);
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;  // warp-uniform
+    uint32_t i = base + lane;
+    bool valid = false;
+    uint32_t cell = 0, lq = 0;
+    if (i < n) {
+        float4 h = __ldg(hits + i);
+        uint32_t tri = __float_as_uint(h.w);
+        if (tri != kMiss && isfinite(h.x)) {
+            float4 o = __ldg(o_tmin + i);
+            float4 d = __ldg(d_tmax + i);
+            uint32_t qo[3], qd[3];
+            float dh[3];
+            quantise_ray(f, o, d, qo, qd, dh);
+            cell = table_cell(qo, qd);
+            float len = __fmul_rn(h.x, length3(d.x, d.y, d.z));
+            float x = __fmul_rn(len, invE);
+            if (!(x > 0.0f)) x = 0.0f;
+            if (x > 64.0f) x = 64.0f;
+            lq = __float2uint_rz(__fmul_rn(x, 16777216.0f));
+            valid = true;
+        }
+    }
+    uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
+    if (!valid) return;
+    uint32_t peers = __match_any_sync(vmask, cell);
+    uint32_t s_hi = __reduce_add_sync(peers, lq >> 16);
+    uint32_t s_lo = __reduce_add_sync(peers, lq & 0xFFFFu);
+    if (lane == (uint32_t)(__ffs(peers) - 1)) {
+        unsigned long long sum = ((unsigned long long)s_hi << 16) + s_lo;
+        atomicAdd(cells + 2 * (size_t)cell, sum);
+        atomicAdd(cells + 2 * (size_t)cell + 1, (unsigned long long)__popc(peers));
+    }
+}
+
+static bool box_ok(const float lo[3], const float hi[3]) {
+    for (int c = 0; c < 3; ++c)
+        if (!std::isfinite(lo[c]) || !std::isfinite(hi[c]) || !(lo[c] <= hi[c])) return false;
+    return true;
+}
+
+static float largest_extent_host(const Box &b) {
+    float e = b.hi[0] - b.lo[0];
+    for (int c = 1; c < 3; ++c) {
+        float x = b.hi[c] - b.lo[c];
+        if (x > e) e = x;
+    }
+    return e;
+}
+
+}  // namespace rr
+
+using namespace rr;
+
+extern "C" rr_status rr_compute_keys(const float *o_tmin, const float *d_tmax, uint32_t n,
+                                     const rr_key_params *p, void *keys_out, void *stream) {
+    if (!p) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: params is NULL");
+    if (p->layout > RR_KEY_TWO_POINT) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: bad layout");
+    if (p->bits < 1 || p->bits > 64) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: bits not in 1..64");
+    if (p->layout == RR_KEY_TWO_POINT && p->t_source > RR_T_GIVEN)
+        return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: bad t_source");
+    if (!box_ok(p->aabb_lo, p->aabb_hi)) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: bad box");
+    if (n == 0) return RR_OK;
+    if (!o_tmin || !d_tmax || !keys_out) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: NULL buffer");
+    if (!aligned16(o_tmin) || !aligned16(d_tmax))
+        return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: rays not 16-byte aligned");
+    const bool wide = p->bits > 32;
+    if (!aligned(keys_out, wide ? 8 : 4)) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: keys misaligned");
+    KeyArgs a;
+    a.o_tmin = reinterpret_cast<const float4 *>(o_tmin);
+    a.d_tmax = reinterpret_cast<const float4 *>(d_tmax);
+    a.n = n;
+    a.bits = p->bits;
+    for (int c = 0; c < 3; ++c) {
+        a.lo[c] = p->aabb_lo[c];
+        a.hi[c] = p->aabb_hi[c];
+    }
+    a.ratio = p->ratio;
+    a.t_given = p->t_given;
+    a.table = nullptr;
+    a.keys = keys_out;
+    rr_status st;
+    if (!device_state(&st)) return st;
+    cudaStream_t s = as_stream(stream);
+    if (p->layout == RR_KEY_AILA) {
+        launch_keys<RR_KEY_AILA, 0>(a, wide, s);
+    } else if (p->layout == RR_KEY_AILA_COMPACT) {
+        launch_keys<RR_KEY_AILA_COMPACT, 0>(a, wide, s);
+    } else if (p->t_source == RR_T_FIXED) {
+        if (!std::isfinite(p->ratio)) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: ratio not finite");
+        launch_keys<RR_KEY_TWO_POINT, RR_T_FIXED>(a, wide, s);
+    } else if (p->t_source == RR_T_GIVEN) {
+        if (!p->t_given || !aligned(p->t_given, 4))
+            return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: t_given missing or misaligned");
+        launch_keys<RR_KEY_TWO_POINT, RR_T_GIVEN>(a, wide, s);
+    } else {
+        const rr_length_table *t = p->table;
+        if (!t) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: ADAPTIVE needs a table");
+        if (std::memcmp(t->box.lo, p->aabb_lo, sizeof(float) * 3) ||
+            std::memcmp(t->box.hi, p->aabb_hi, sizeof(float) * 3))
+            return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: table was created for another box");
+        a.table = reinterpret_cast<const ulonglong2 *>(t->cells);
+        launch_keys<RR_KEY_TWO_POINT, RR_T_ADAPTIVE>(a, wide, s);
+    }
+    note_launches(1);
+    return check_launch("rr_compute_keys");
+}
+
+extern "C" rr_status rr_length_table_create(const float lo[3], const float hi[3], rr_length_table **out,
+                                            void *stream) {
+    if (!out || !lo || !hi) return fail(RR_ERR_INVALID_ARG, "rr_length_table_create: NULL argument");
+    *out = nullptr;
+    if (!box_ok(lo, hi)) return fail(RR_ERR_INVALID_ARG, "rr_length_table_create: bad box");
+    rr_status st;
+    if (!device_state(&st)) return st;
+    rr_length_table *t = new rr_length_table();
+    cudaGetDevice(&t->device);
+    for (int c = 0; c < 3; ++c) {
+        t->box.lo[c] = lo[c];
+        t->box.hi[c] = hi[c];
+    }
+    t->E = largest_extent_host(t->box);
+    if (!(t->E > 0.0f)) {
+        delete t;
+        return fail(RR_ERR_INVALID_ARG, "rr_length_table_create: box has zero extent");
+    }
+    cudaError_t e = cudaMalloc(&t->cells, sizeof(unsigned long long) * 2 * kTableCells);
+    if (e != cudaSuccess) {
+        delete t;
+        cudaGetLastError();
+        return fail(RR_ERR_OOM, "rr_length_table_create: cudaMalloc failed");
+    }
+    *out = t;
+    return rr_length_table_reset(t, stream);
+}
+
+extern "C" rr_status rr_length_table_reset(rr_length_table *t, void *stream) {
+    if (!t) return fail(RR_ERR_INVALID_ARG, "rr_length_table_reset: NULL table");
+    table_init_kernel<<<kTableCells / 256, 256, 0, as_stream(stream)>>>(reinterpret_cast<ulonglong2 *>(t->cells));
+    note_launches(1);
+    return check_launch("rr_length_table_reset");
+}
+
+extern "C" rr_status rr_length_table_accumulate(rr_length_table *t, const float *o_tmin, const float *d_tmax,
+                                                const float *hits, uint32_t n, void *stream) {
+    if (!t) return fail(RR_ERR_INVALID_ARG, "rr_length_table_accumulate: NULL table");
+    if (n == 0) return RR_OK;
+    if (!o_tmin || !d_tmax || !hits) return fail(RR_ERR_INVALID_ARG, "rr_length_table_accumulate: NULL buffer");
+    if (!aligned16(o_tmin) || !aligned16(d_tmax) || !aligned16(hits))
+        return fail(RR_ERR_INVALID_ARG, "rr_length_table_accumulate: buffers not 16-byte aligned");
+    dim3 grid((n + 255) / 256);
+    table_accumulate_kernel<<<grid, 256, 0, as_stream(stream)>>>(
+        t->cells, t->box.lo[0], t->box.lo[1], t->box.lo[2], t->box.hi[0], t->box.hi[1], t->box.hi[2],
+        reinterpret_cast<const float4 *>(o_tmin), reinterpret_cast<const float4 *>(d_tmax),
+        reinterpret_cast<const float4 *>(hits), n);
+    note_launches(1);
+    return check_launch("rr_length_table_accumulate");
+}
+
+extern "C" rr_status rr_length_table_read(const rr_length_table *t, uint64_t *sum_host, uint32_t *cnt_host) {
+    if (!t || !sum_host || !cnt_host) return fail(RR_ERR_INVALID_ARG, "rr_length_table_read: NULL argument");
+    unsigned long long *tmp = new (std::nothrow) unsigned long long[2 * (size_t)kTableCells];
+    if (!tmp) return fail(RR_ERR_OOM, "rr_length_table_read: host allocation failed");
+    cudaError_t e = cudaMemcpy(tmp, t->cells, sizeof(unsigned long long) * 2 * kTableCells, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        delete[] tmp;
+        return fail_cuda(e, "rr_length_table_read");
+    }
+    for (uint32_t i = 0; i < kTableCells; ++i) {
+        sum_host[i] = tmp[2 * (size_t)i];
+        cnt_host[i] = (uint32_t)tmp[2 * (size_t)i + 1];
+    }
+    delete[] tmp;
+    return RR_OK;
+}
+
+extern "C" rr_status rr_length_table_write(rr_length_table *t, const uint64_t *sum_host, const uint32_t *cnt_host) {
+    if (!t || !sum_host || !cnt_host) return fail(RR_ERR_INVALID_ARG, "rr_length_table_write: NULL argument");
+    unsigned long long *tmp = new (std::nothrow) unsigned long long[2 * (size_t)kTableCells];
+    if (!tmp) return fail(RR_ERR_OOM, "rr_length_table_write: host allocation failed");
+    for (uint32_t i = 0; i < kTableCells; ++i) {
+        tmp[2 * (size_t)i] = sum_host[i];
+        tmp[2 * (size_t)i + 1] = cnt_host[i];
+    }
+    cudaError_t e = cudaMemcpy(t->cells, tmp, sizeof(unsigned long long) * 2 * kTableCells, cudaMemcpyHostToDevice);
+    delete[] tmp;
+    if (e != cudaSuccess) return fail_cuda(e, "rr_length_table_write");
+    return RR_OK;
+}
+
+extern "C" rr_status rr_length_table_destroy(rr_length_table *t) {
+    if (!t) return RR_OK;
+    cudaFree(t->cells);
+    delete t;
+    return RR_OK;
+}

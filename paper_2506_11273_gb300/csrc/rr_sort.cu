@@ -1,0 +1,373 @@
+// Stable LSD radix sort of (key, index) pairs (Section 3.2), onesweep style:
+// one upfront pass builds the digit histograms of every pass; then each
+// digit pass is a single kernel in which a tile ranks its keys with warp
+// match_any, publishes its per-digit counts, resolves its global offsets by a
+// decoupled look-back over the preceding tiles, and scatters through shared
+// memory so that global writes come out in runs.
+#include <algorithm>
+
+#include "rr_common.cuh"
+
+namespace rr {
+
+constexpr uint32_t kFlagAgg = 1u << 30;     // word holds this tile's count only
+constexpr uint32_t kFlagPrefix = 2u << 30;  // word holds the count of tiles 0..this
+constexpr uint32_t kValMask = (1u << 30) - 1u;
+constexpr uint32_t kSpinLimit = 1u << 20;   // bounded wait on a predecessor's word
+constexpr int kSortBlock = 256;
+constexpr int kSortWarps = kSortBlock / 32;
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <typename K>
+struct SortTile;
+template <>
+struct SortTile<uint32_t> {
+    static constexpr int kItems = 16;
+};
+template <>
+struct SortTile<unsigned long long> {
+    static constexpr int kItems = 12;
+};
+
+template <typename K>
+__device__ __forceinline__ uint32_t digit_of(K k, uint32_t shift, uint32_t mask) {
+    return (uint32_t)(k >> shift) & mask;
+}
+
+// Exclusive scan of one value per thread over the first `RADIX` threads
+// (threads beyond contribute zero).  Called by every thread of the block.
+template <int RADIX>
+__device__ __forceinline__ uint32_t scan_digits(uint32_t v, uint32_t *s_warp) {
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    if (RADIX > 32) {
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        uint32_t add = 0;
+        for (uint32_t w = 0; w < warp; ++w) add += s_warp[w];
+        __syncthreads();
+        x += add;
+    }
+    return x - v;
+}
+
+// ------------------------------------------------------------------ upfront histograms
+
+template <typename K, int RBITS>
+__global__ void __launch_bounds__(kSortBlock) sort_histogram_kernel(const K *__restrict__ keys, uint32_t n,
+                                                                   uint32_t bits, uint32_t passes,
+                                                                   uint32_t *__restrict__ hist,
+                                                                   uint4 *__restrict__ zero_words,
+                                                                   size_t zero_count) {
+    constexpr int RADIX = 1 << RBITS;
+    constexpr int PMAX = (64 + RBITS - 1) / RBITS;
+    __shared__ uint32_t sh[PMAX * RADIX];
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint32_t i = threadIdx.x; i < PMAX * RADIX; i += kSortBlock) sh[i] = 0;
+    __syncthreads();
+    const uint32_t stride = gridDim.x * kSortBlock;
+    for (uint32_t base = blockIdx.x * kSortBlock + (threadIdx.x & ~31u); base < n; base += stride) {
+        const uint32_t i = base + lane;
+        const bool valid = i < n;
+        const uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
+        if (valid) {
+            const K k = keys[i];
+            for (uint32_t p = 0; p < passes; ++p) {
+                const uint32_t shift = p * RBITS;
+                const uint32_t nb = min((uint32_t)RBITS, bits - shift);
+                const uint32_t dg = digit_of(k, shift, (1u << nb) - 1u);
+                const uint32_t peers = __match_any_sync(vmask, dg);
+                if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sh[p * RADIX + dg], __popc(peers));
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < passes * RADIX; i += kSortBlock)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+    // the look-back words of every pass start at zero
+    for (size_t i = (size_t)blockIdx.x * kSortBlock + threadIdx.x; i < zero_count; i += stride)
+        zero_words[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// ------------------------------------------------------------------ one digit pass
+
+template <typename K>
+struct PassArgs {
+    const K *keys_in;
+    const uint32_t *vals_in;  // null on the first pass: the value is the input index
+    K *keys_out;              // null: keys are not written
+    uint32_t *vals_out;
+    uint32_t n;
+    uint32_t shift;
+    uint32_t mask;
+    const uint32_t *hist;     // RADIX counts of this pass's digit over all keys
+    uint32_t *lookback;       // [tiles][RADIX]
+    uint32_t *tile_counter;
+    uint32_t *err;
+};
+
+template <typename K, int RBITS>
+__global__ void __launch_bounds__(kSortBlock) onesweep_kernel(PassArgs<K> a) {
+    constexpr int RADIX = 1 << RBITS;
+    constexpr int ITEMS = SortTile<K>::kItems;
+    constexpr int TILE = kSortBlock * ITEMS;
+    constexpr int WTILE = 32 * ITEMS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    K *s_keys = reinterpret_cast<K *>(smem_raw);
+    uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + TILE);
+    uint32_t *s_wh = s_vals + TILE;                // [warps][RADIX]: counts, then prefix over warps
+    uint32_t *s_lstart = s_wh + kSortWarps * RADIX;  // tile-local start of each digit
+    uint32_t *s_gbase = s_lstart + RADIX;          // global position minus tile-local position
+    uint32_t *s_misc = s_gbase + RADIX;            // [0] tile id, [8..15] scan scratch
+
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    if (tid == 0) s_misc[0] = atomicAdd(a.tile_counter, 1u);
+    for (uint32_t i = tid; i < kSortWarps * RADIX; i += kSortBlock) s_wh[i] = 0;
+    __syncthreads();
+    const uint32_t tile = s_misc[0];
+    const uint32_t base = tile * TILE;
+    const uint32_t wbase = base + warp * WTILE;
+
+    K k[ITEMS];
+    uint32_t v[ITEMS], r[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t idx = wbase + j * 32 + lane;
+        if (idx < a.n) {
+            k[j] = a.keys_in[idx];
+            v[j] = a.vals_in ? a.vals_in[idx] : idx;
+        } else {
+            k[j] = 0;
+            v[j] = 0;
+        }
+    }
+    // stable rank inside the warp: items in index order (j, then lane)
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const bool valid = wbase + j * 32 + lane < a.n;
+        const uint32_t dg = valid ? digit_of(k[j], a.shift, a.mask) : (uint32_t)RADIX;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg);
+        const uint32_t cur = valid ? s_wh[warp * RADIX + dg] : 0u;
+        __syncwarp();
+        if (valid && lane == 31u - __clz(peers)) s_wh[warp * RADIX + dg] = cur + __popc(peers);
+        __syncwarp();
+        r[j] = cur + __popc(peers & lt);
+    }
+    __syncthreads();
+
+    // per digit: prefix over warps and the tile's count, published at once
+    uint32_t cnt = 0;
+    if (tid < RADIX) {
+        for (int w = 0; w < kSortWarps; ++w) {
+            const uint32_t c = s_wh[w * RADIX + tid];
+            s_wh[w * RADIX + tid] = cnt;
+            cnt += c;
+        }
+        st_relaxed(a.lookback + (size_t)tile * RADIX + tid, (tile == 0 ? kFlagPrefix : kFlagAgg) | cnt);
+    }
+    const uint32_t dstart = scan_digits<RADIX>(tid < RADIX ? a.hist[tid] : 0u, s_misc + 8);
+    const uint32_t lstart = scan_digits<RADIX>(cnt, s_misc + 8);
+    if (tid < RADIX) {
+        uint32_t excl = 0;
+        if (tile > 0) {
+            // decoupled look-back: add predecessors' counts until one holds a prefix
+            uint32_t j = tile - 1, spins = 0;
+            while (true) {
+                const uint32_t w = ld_relaxed(a.lookback + (size_t)j * RADIX + tid);
+                const uint32_t fl = w & ~kValMask;
+                if (fl == 0u) {
+                    if (++spins > kSpinLimit) {
+                        atomicOr(a.err, RR_DEVERR_LOOKBACK_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(32);
+                    continue;
+                }
+                excl += w & kValMask;
+                if (fl == kFlagPrefix || j == 0) break;
+                --j;
+            }
+            st_relaxed(a.lookback + (size_t)tile * RADIX + tid, kFlagPrefix | ((excl + cnt) & kValMask));
+        }
+        s_lstart[tid] = lstart;
+        s_gbase[tid] = dstart + excl - lstart;
+    }
+    __syncthreads();
+
+    // scatter into shared memory in digit order (stable)
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        if (wbase + j * 32 + lane < a.n) {
+            const uint32_t dg = digit_of(k[j], a.shift, a.mask);
+            const uint32_t pos = s_lstart[dg] + s_wh[warp * RADIX + dg] + r[j];
+            s_keys[pos] = k[j];
+            s_vals[pos] = v[j];
+        }
+    }
+    __syncthreads();
+    const uint32_t tile_n = min((uint32_t)TILE, a.n - base);
+    for (uint32_t i = tid; i < tile_n; i += kSortBlock) {
+        const K key = s_keys[i];
+        const uint32_t gpos = s_gbase[digit_of(key, a.shift, a.mask)] + i;
+        if (a.keys_out) a.keys_out[gpos] = key;
+        a.vals_out[gpos] = s_vals[i];
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct SortPlan {
+    uint32_t passes, radix, tiles, kb;
+    size_t off_hist, off_counters, off_lookback, off_keys_a, off_keys_b, off_vals, total;
+};
+
+static SortPlan plan_sort(uint32_t n, uint32_t bits, uint32_t radix_bits) {
+    SortPlan p;
+    p.passes = (bits + radix_bits - 1) / radix_bits;
+    p.radix = 1u << radix_bits;
+    p.kb = bits > 32 ? 8u : 4u;
+    const uint32_t tile = kSortBlock * (bits > 32 ? SortTile<unsigned long long>::kItems : SortTile<uint32_t>::kItems);
+    p.tiles = (n + tile - 1) / tile;
+    size_t off = 0;
+    p.off_hist = off;
+    off = align256(off + sizeof(uint32_t) * p.passes * p.radix);
+    p.off_counters = off;
+    off = align256(off + sizeof(uint32_t) * p.passes);
+    p.off_lookback = off;
+    off = align256(off + sizeof(uint32_t) * (size_t)p.passes * p.tiles * p.radix);
+    p.off_keys_a = off;
+    off = align256(off + (size_t)p.kb * n);
+    p.off_keys_b = off;
+    off = align256(off + (size_t)p.kb * n);
+    p.off_vals = off;
+    off = align256(off + sizeof(uint32_t) * (size_t)n);
+    p.total = off;
+    return p;
+}
+
+template <typename K, int RBITS>
+static size_t pass_smem() {
+    constexpr int RADIX = 1 << RBITS;
+    constexpr int TILE = kSortBlock * SortTile<K>::kItems;
+    return sizeof(K) * TILE + sizeof(uint32_t) * (TILE + kSortWarps * RADIX + 2 * RADIX + 16);
+}
+
+template <typename K, int RBITS>
+static rr_status run_sort(const SortPlan &pl, const K *keys_in, K *keys_out, uint32_t *perm_out, uint32_t n,
+                          uint32_t bits, unsigned char *ws, uint32_t *err, int sm_count, cudaStream_t s) {
+    uint32_t *hist = reinterpret_cast<uint32_t *>(ws + pl.off_hist);
+    uint32_t *counters = reinterpret_cast<uint32_t *>(ws + pl.off_counters);
+    uint32_t *lookback = reinterpret_cast<uint32_t *>(ws + pl.off_lookback);
+    K *keys_a = reinterpret_cast<K *>(ws + pl.off_keys_a);
+    K *keys_b = reinterpret_cast<K *>(ws + pl.off_keys_b);
+    uint32_t *vals_ws = reinterpret_cast<uint32_t *>(ws + pl.off_vals);
+
+    cudaError_t e = cudaMemsetAsync(ws, 0, pl.off_lookback, s);
+    if (e != cudaSuccess) return fail_cuda(e, "rr_sort: memset");
+    const size_t zero_count = (size_t)pl.passes * pl.tiles * pl.radix / 4;
+    const uint32_t hist_blocks =
+        std::max(1u, std::min((n + kSortBlock - 1) / kSortBlock, (uint32_t)sm_count * 4u));
+    sort_histogram_kernel<K, RBITS><<<hist_blocks, kSortBlock, 0, s>>>(
+        keys_in, n, bits, pl.passes, hist, reinterpret_cast<uint4 *>(lookback), zero_count);
+    const size_t smem = pass_smem<K, RBITS>();
+    const K *kin = keys_in;
+    const uint32_t *vin = nullptr;
+    for (uint32_t p = 0; p < pl.passes; ++p) {
+        const bool final_slot = ((pl.passes - 1 - p) & 1u) == 0;
+        K *kout;
+        if (p == pl.passes - 1)
+            kout = keys_out;
+        else
+            kout = final_slot ? (keys_out ? keys_out : keys_b) : keys_a;
+        uint32_t *vout = final_slot ? perm_out : vals_ws;
+        PassArgs<K> a;
+        a.keys_in = kin;
+        a.vals_in = vin;
+        a.keys_out = kout;
+        a.vals_out = vout;
+        a.n = n;
+        a.shift = p * RBITS;
+        const uint32_t nb = std::min<uint32_t>(RBITS, bits - p * RBITS);
+        a.mask = (1u << nb) - 1u;
+        a.hist = hist + p * pl.radix;
+        a.lookback = lookback + (size_t)p * pl.tiles * pl.radix;
+        a.tile_counter = counters + p;
+        a.err = err;
+        onesweep_kernel<K, RBITS><<<pl.tiles, kSortBlock, smem, s>>>(a);
+        kin = kout;
+        vin = vout;
+    }
+    note_launches(1 + pl.passes);
+    return check_launch("rr_sort");
+}
+
+}  // namespace rr
+
+using namespace rr;
+
+extern "C" rr_status rr_sort_workspace_size(uint32_t n, uint32_t bits, uint32_t radix_bits, size_t *bytes) {
+    if (!bytes) return fail(RR_ERR_INVALID_ARG, "rr_sort_workspace_size: bytes is NULL");
+    if (bits < 1 || bits > 64) return fail(RR_ERR_INVALID_ARG, "rr_sort_workspace_size: bits not in 1..64");
+    if (radix_bits != 4 && radix_bits != 8)
+        return fail(RR_ERR_INVALID_ARG, "rr_sort_workspace_size: radix_bits must be 4 or 8");
+    if (n >= (1u << 30)) return fail(RR_ERR_INVALID_ARG, "rr_sort_workspace_size: n must be < 2^30");
+    *bytes = plan_sort(n, bits, radix_bits).total;
+    return RR_OK;
+}
+
+extern "C" rr_status rr_sort(const void *keys_in, void *keys_out, uint32_t *perm_out, uint32_t n, uint32_t bits,
+                             uint32_t radix_bits, void *workspace, size_t workspace_bytes, void *stream) {
+    if (bits < 1 || bits > 64) return fail(RR_ERR_INVALID_ARG, "rr_sort: bits not in 1..64");
+    if (radix_bits != 4 && radix_bits != 8) return fail(RR_ERR_INVALID_ARG, "rr_sort: radix_bits must be 4 or 8");
+    if (n >= (1u << 30)) return fail(RR_ERR_INVALID_ARG, "rr_sort: n must be < 2^30");
+    if (n == 0) return RR_OK;
+    if (!keys_in || !perm_out || !workspace) return fail(RR_ERR_INVALID_ARG, "rr_sort: NULL buffer");
+    const SortPlan pl = plan_sort(n, bits, radix_bits);
+    if (workspace_bytes < pl.total) return fail(RR_ERR_INVALID_ARG, "rr_sort: workspace too small");
+    if (!aligned(workspace, 256)) return fail(RR_ERR_INVALID_ARG, "rr_sort: workspace not 256-byte aligned");
+    const size_t kbytes = (size_t)pl.kb * n;
+    if (!aligned(keys_in, pl.kb) || (keys_out && !aligned(keys_out, pl.kb)) || !aligned(perm_out, 4))
+        return fail(RR_ERR_INVALID_ARG, "rr_sort: misaligned buffer");
+    if (overlaps(keys_in, kbytes, perm_out, 4ull * n) ||
+        (keys_out && (overlaps(keys_out, kbytes, keys_in, kbytes) || overlaps(keys_out, kbytes, perm_out, 4ull * n))) ||
+        overlaps(workspace, pl.total, keys_in, kbytes) || overlaps(workspace, pl.total, perm_out, 4ull * n) ||
+        (keys_out && overlaps(workspace, pl.total, keys_out, kbytes)))
+        return fail(RR_ERR_INVALID_ARG, "rr_sort: buffers overlap");
+    rr_status st;
+    DeviceState *ds = device_state(&st);
+    if (!ds) return st;
+    cudaStream_t s = as_stream(stream);
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    if (pl.kb == 4) {
+        const uint32_t *ki = static_cast<const uint32_t *>(keys_in);
+        uint32_t *ko = static_cast<uint32_t *>(keys_out);
+        return radix_bits == 8 ? run_sort<uint32_t, 8>(pl, ki, ko, perm_out, n, bits, ws, ds->err, ds->sm_count, s)
+                               : run_sort<uint32_t, 4>(pl, ki, ko, perm_out, n, bits, ws, ds->err, ds->sm_count, s);
+    }
+    const unsigned long long *ki = static_cast<const unsigned long long *>(keys_in);
+    unsigned long long *ko = static_cast<unsigned long long *>(keys_out);
+    return radix_bits == 8
+               ? run_sort<unsigned long long, 8>(pl, ki, ko, perm_out, n, bits, ws, ds->err, ds->sm_count, s)
+               : run_sort<unsigned long long, 4>(pl, ki, ko, perm_out, n, bits, ws, ds->err, ds->sm_count, s);
+}

@@ -1,0 +1,365 @@
+"""Thin Python binding of librr's C ABI (include/rr.h).
+
+Functions carry the C names and only marshal arguments: torch CUDA tensors
+become device pointers, the current torch stream becomes the cudaStream_t.
+Every step of the pipeline runs in librr's kernels.  There is no fallback:
+if librr.so is missing or fails to load, every call raises.
+
+Storage dtypes: uint32 buffers are torch.int32 tensors and uint64 keys are
+torch.int64 tensors (same bits); use ``.view(numpy.uint32/uint64)`` on the
+host side.  Rays are float32 [N,4] tensors (o_tmin, d_tmax), hits float32 [N,4]
+(t, u, v, triangle id bits).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librr.so")
+_lock = threading.Lock()
+_lib = None
+
+RR_KEY_AILA, RR_KEY_AILA_COMPACT, RR_KEY_TWO_POINT = 0, 1, 2
+RR_T_FIXED, RR_T_ADAPTIVE, RR_T_GIVEN = 0, 1, 2
+RR_DEVERR_LOOKBACK_TIMEOUT = 0x1
+RR_DEVERR_TRACE_STACK = 0x2
+MISS = 0xFFFFFFFF
+TABLE_CELLS = 1 << 20
+
+STATUS = {0: "RR_OK", 1: "RR_ERR_INVALID_ARG", 2: "RR_ERR_CUDA", 3: "RR_ERR_OOM",
+          4: "RR_ERR_TIMEOUT", 5: "RR_ERR_STACK", 6: "RR_ERR_UNSUPPORTED"}
+
+# every symbol include/rr.h declares
+EXPORTS = [
+    "rr_compute_keys", "rr_sort_workspace_size", "rr_sort", "rr_permute", "rr_build_bvh",
+    "rr_bvh_destroy", "rr_bvh_get_info", "rr_trace", "rr_length_table_create",
+    "rr_length_table_reset", "rr_length_table_accumulate", "rr_length_table_read",
+    "rr_length_table_write", "rr_length_table_destroy", "rr_pipeline_create",
+    "rr_pipeline_destroy", "rr_pipeline_run", "rr_pipeline_run_host", "rr_device_error",
+    "rr_status_string", "rr_last_error_message", "rr_kernel_launch_count",
+]
+
+
+class RRError(RuntimeError):
+    def __init__(self, status: int, what: str, msg: str):
+        super().__init__("%s: %s (%s)" % (what, STATUS.get(status, status), msg))
+        self.status = status
+
+
+class KeyParams(C.Structure):
+    _fields_ = [("layout", C.c_uint32), ("bits", C.c_uint32), ("t_source", C.c_uint32),
+                ("ratio", C.c_float), ("aabb_lo", C.c_float * 3), ("aabb_hi", C.c_float * 3),
+                ("t_given", C.c_void_p), ("table", C.c_void_p)]
+
+
+class BvhInfo(C.Structure):
+    _fields_ = [("n_tris", C.c_uint32), ("n_nodes", C.c_uint32), ("n_leaves", C.c_uint32),
+                ("depth", C.c_uint32), ("node_bytes", C.c_uint64), ("tri_bytes", C.c_uint64),
+                ("aabb_lo", C.c_float * 3), ("aabb_hi", C.c_float * 3),
+                ("build_seconds", C.c_double)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("librr.so is not built (%s); run __graft_entry__.build() or "
+                                   "python paper_2506_11273_gb300/build.py" % LIB_PATH)
+            L = C.CDLL(LIB_PATH)
+            vp, u32, i32 = C.c_void_p, C.c_uint32, C.c_int
+            L.rr_compute_keys.argtypes = [vp, vp, u32, C.POINTER(KeyParams), vp, vp]
+            L.rr_sort_workspace_size.argtypes = [u32, u32, u32, C.POINTER(C.c_size_t)]
+            L.rr_sort.argtypes = [vp, vp, vp, u32, u32, u32, vp, C.c_size_t, vp]
+            L.rr_permute.argtypes = [vp, vp, vp, vp, u32, vp, vp, vp, vp]
+            L.rr_build_bvh.argtypes = [vp, u32, C.POINTER(vp)]
+            L.rr_bvh_destroy.argtypes = [vp]
+            L.rr_bvh_get_info.argtypes = [vp, C.POINTER(BvhInfo)]
+            L.rr_trace.argtypes = [vp, vp, vp, u32, vp, vp]
+            L.rr_length_table_create.argtypes = [C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                                 C.POINTER(vp), vp]
+            L.rr_length_table_reset.argtypes = [vp, vp]
+            L.rr_length_table_accumulate.argtypes = [vp, vp, vp, vp, u32, vp]
+            L.rr_length_table_read.argtypes = [vp, vp, vp]
+            L.rr_length_table_write.argtypes = [vp, vp, vp]
+            L.rr_length_table_destroy.argtypes = [vp]
+            L.rr_pipeline_create.argtypes = [vp, u32, C.POINTER(KeyParams), u32, C.POINTER(vp)]
+            L.rr_pipeline_destroy.argtypes = [vp]
+            L.rr_pipeline_run.argtypes = [vp, vp, vp, vp, u32, vp, vp, vp]
+            L.rr_pipeline_run_host.argtypes = [vp, vp, vp, vp, u32, vp, vp, vp]
+            L.rr_device_error.argtypes = [C.POINTER(C.c_uint32)]
+            L.rr_status_string.argtypes = [i32]
+            L.rr_status_string.restype = C.c_char_p
+            L.rr_last_error_message.argtypes = []
+            L.rr_last_error_message.restype = C.c_char_p
+            L.rr_kernel_launch_count.argtypes = []
+            L.rr_kernel_launch_count.restype = C.c_uint64
+            _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        msg = lib().rr_last_error_message().decode(errors="replace")
+        raise RRError(status, what, msg)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _hptr(t) -> int | None:
+    """Host pointer of a numpy array or a CPU (ideally pinned) torch tensor."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("expected a contiguous array")
+        return t.ctypes.data
+    if t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CPU tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+# ---------------------------------------------------------------- keys
+
+def key_params(layout: int, bits: int, aabb_lo, aabb_hi, t_source: int = RR_T_FIXED,
+               ratio: float = 0.25, t_given=None, table: "LengthTable | None" = None) -> KeyParams:
+    p = KeyParams()
+    p.layout, p.bits, p.t_source, p.ratio = layout, bits, t_source, float(np.float32(ratio))
+    for c in range(3):
+        p.aabb_lo[c] = float(np.float32(aabb_lo[c]))
+        p.aabb_hi[c] = float(np.float32(aabb_hi[c]))
+    p.t_given = _ptr(t_given)
+    p.table = table.handle if table is not None else None
+    p._keep = (t_given, table)  # keep referenced objects alive with the struct
+    return p
+
+
+def rr_compute_keys(o_tmin, d_tmax, params: KeyParams, keys_out, n: int | None = None, stream=None):
+    n = o_tmin.shape[0] if n is None else n
+    _check(lib().rr_compute_keys(_ptr(o_tmin), _ptr(d_tmax), n, C.byref(params), _ptr(keys_out),
+                                 _stream(stream)), "rr_compute_keys")
+
+
+# ---------------------------------------------------------------- sort
+
+def rr_sort_workspace_size(n: int, bits: int, radix_bits: int = 8) -> int:
+    b = C.c_size_t()
+    _check(lib().rr_sort_workspace_size(n, bits, radix_bits, C.byref(b)), "rr_sort_workspace_size")
+    return int(b.value)
+
+
+def rr_sort(keys_in, keys_out, perm_out, n: int, bits: int, radix_bits: int, workspace,
+            stream=None):
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib().rr_sort(_ptr(keys_in), _ptr(keys_out), _ptr(perm_out), n, bits, radix_bits,
+                         _ptr(workspace), nbytes, _stream(stream)), "rr_sort")
+
+
+def sort_workspace(n: int, bits: int, radix_bits: int = 8, device="cuda") -> torch.Tensor:
+    size = rr_sort_workspace_size(n, bits, radix_bits)
+    # torch's caching allocator returns 512-byte aligned blocks
+    return torch.empty(max(size, 256), dtype=torch.uint8, device=device)
+
+
+# ---------------------------------------------------------------- reorder
+
+def rr_permute(o_tmin_in, d_tmax_in, payload_in, perm, o_tmin_out, d_tmax_out, payload_out,
+               n: int | None = None, stream=None):
+    n = perm.shape[0] if n is None else n
+    _check(lib().rr_permute(_ptr(o_tmin_in), _ptr(d_tmax_in), _ptr(payload_in), _ptr(perm), n,
+                            _ptr(o_tmin_out), _ptr(d_tmax_out), _ptr(payload_out),
+                            _stream(stream)), "rr_permute")
+
+
+# ---------------------------------------------------------------- BVH and trace
+
+class BVH:
+    """Owner of an rr_bvh handle built from a host triangle soup [T,9] float32."""
+
+    def __init__(self, tris: np.ndarray):
+        tris = np.ascontiguousarray(tris, dtype=np.float32).reshape(-1, 9)
+        self.n_tris = tris.shape[0]
+        h = C.c_void_p()
+        _check(lib().rr_build_bvh(tris.ctypes.data if self.n_tris else None, self.n_tris,
+                                  C.byref(h)), "rr_build_bvh")
+        self.handle = h.value
+
+    def info(self) -> BvhInfo:
+        i = BvhInfo()
+        _check(lib().rr_bvh_get_info(self.handle, C.byref(i)), "rr_bvh_get_info")
+        return i
+
+    def aabb(self):
+        i = self.info()
+        return (np.array(list(i.aabb_lo), np.float32), np.array(list(i.aabb_hi), np.float32))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rr_bvh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rr_build_bvh(tris: np.ndarray) -> BVH:
+    return BVH(tris)
+
+
+def rr_trace(bvh: BVH, o_tmin, d_tmax, hits_out, n: int | None = None, stream=None):
+    n = o_tmin.shape[0] if n is None else n
+    _check(lib().rr_trace(bvh.handle, _ptr(o_tmin), _ptr(d_tmax), n, _ptr(hits_out),
+                          _stream(stream)), "rr_trace")
+
+
+# ---------------------------------------------------------------- ray-length table
+
+class LengthTable:
+    """Owner of an rr_length_table (2^20 cells) for one scene box."""
+
+    def __init__(self, aabb_lo, aabb_hi, stream=None):
+        lo = (C.c_float * 3)(*[float(np.float32(x)) for x in aabb_lo])
+        hi = (C.c_float * 3)(*[float(np.float32(x)) for x in aabb_hi])
+        h = C.c_void_p()
+        _check(lib().rr_length_table_create(lo, hi, C.byref(h), _stream(stream)),
+               "rr_length_table_create")
+        self.handle = h.value
+
+    def reset(self, stream=None):
+        _check(lib().rr_length_table_reset(self.handle, _stream(stream)), "rr_length_table_reset")
+
+    def accumulate(self, o_tmin, d_tmax, hits, n: int | None = None, stream=None):
+        rr_length_table_accumulate(self, o_tmin, d_tmax, hits, n, stream)
+
+    def read(self):
+        s = np.zeros(TABLE_CELLS, np.uint64)
+        c = np.zeros(TABLE_CELLS, np.uint32)
+        _check(lib().rr_length_table_read(self.handle, s.ctypes.data, c.ctypes.data),
+               "rr_length_table_read")
+        return s, c
+
+    def write(self, s: np.ndarray, c: np.ndarray):
+        s = np.ascontiguousarray(s, np.uint64)
+        c = np.ascontiguousarray(c, np.uint32)
+        _check(lib().rr_length_table_write(self.handle, s.ctypes.data, c.ctypes.data),
+               "rr_length_table_write")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rr_length_table_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rr_length_table_accumulate(table: LengthTable, o_tmin, d_tmax, hits, n: int | None = None,
+                               stream=None):
+    n = o_tmin.shape[0] if n is None else n
+    _check(lib().rr_length_table_accumulate(table.handle, _ptr(o_tmin), _ptr(d_tmax), _ptr(hits), n,
+                                            _stream(stream)), "rr_length_table_accumulate")
+
+
+# ---------------------------------------------------------------- one bounce
+
+class Pipeline:
+    """Owner of an rr_pipeline: keys -> sort -> permute -> trace (-> table update)."""
+
+    def __init__(self, bvh: BVH, max_n: int, params: KeyParams, radix_bits: int = 8):
+        h = C.c_void_p()
+        _check(lib().rr_pipeline_create(bvh.handle, max_n, C.byref(params), radix_bits, C.byref(h)),
+               "rr_pipeline_create")
+        self.handle = h.value
+        self._keep = (bvh, params)
+
+    def run(self, o_tmin, d_tmax, payload_in, hits_out, payload_out, n: int | None = None,
+            stream=None):
+        n = o_tmin.shape[0] if n is None else n
+        _check(lib().rr_pipeline_run(self.handle, _ptr(o_tmin), _ptr(d_tmax), _ptr(payload_in), n,
+                                     _ptr(hits_out), _ptr(payload_out), _stream(stream)),
+               "rr_pipeline_run")
+
+    def run_host(self, o_tmin, d_tmax, payload_in, hits_out, payload_out, n: int | None = None,
+                 stream=None):
+        n = o_tmin.shape[0] if n is None else n
+        _check(lib().rr_pipeline_run_host(self.handle, _hptr(o_tmin), _hptr(d_tmax),
+                                          _hptr(payload_in), n, _hptr(hits_out), _hptr(payload_out),
+                                          _stream(stream)), "rr_pipeline_run_host")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rr_pipeline_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- diagnostics
+
+def rr_device_error() -> int:
+    v = C.c_uint32()
+    _check(lib().rr_device_error(C.byref(v)), "rr_device_error")
+    return int(v.value)
+
+
+def rr_kernel_launch_count() -> int:
+    return int(lib().rr_kernel_launch_count())
+
+
+def rr_status_string(s: int) -> str:
+    return lib().rr_status_string(s).decode()
+
+
+# ---------------------------------------------------------------- helpers for callers
+
+def to_device_rays(rays, device="cuda"):
+    """numpy Rays -> (o_tmin, d_tmax, payload) CUDA tensors (payload as int32 bits)."""
+    o = torch.from_numpy(np.ascontiguousarray(rays.o_tmin)).to(device)
+    d = torch.from_numpy(np.ascontiguousarray(rays.d_tmax)).to(device)
+    p = torch.from_numpy(np.ascontiguousarray(rays.payload).view(np.int32)).to(device)
+    return o, d, p
+
+
+def key_dtype(bits: int):
+    return torch.int64 if bits > 32 else torch.int32
+
+
+def keys_to_numpy(t: torch.Tensor) -> np.ndarray:
+    a = t.cpu().numpy()
+    return a.view(np.uint64) if a.dtype == np.int64 else a.view(np.uint32).astype(np.uint64)
+
+
+def u32_to_numpy(t: torch.Tensor) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint32)
