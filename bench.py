@@ -1,0 +1,425 @@
+"""Benchmark of the per-bounce reordered path on the path-tracer workload.
+
+Workload (1920x1080, 1 spp, 4 bounces): the 1,168,576-triangle terrain scene,
+camera rays, then secondary rays scattered off 70% Lambertian / 30% Phong-100
+surfaces with Russian roulette after bounce 2.  The wavefronts are built once
+(untimed) by tracing them in their natural pixel order.  One timed step is one
+pass of the whole hot path over the bounce-3 wavefront:
+
+    Two Point key (adaptive termination estimate, 64 bits)
+    -> stable radix sort (8-bit digits, 8 passes) -> gather of the ray SoA
+    -> closest-hit trace -> length-table update
+
+`value` is rays / step time (MRays/s, inputs resident in HBM, L2 flushed
+between steps).  `unsorted_mrays` traces the same rays in their original
+order; `e2e` runs the same bounce through rr_pipeline_run_host with pinned
+host buffers, copies included.  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "end-to-end MRays/s sorted vs unsorted per bounce; sort GB/s vs HBM peak; p99 latency"
+UNIT = "MRays/s"
+KEY_BITS = 64
+RADIX_BITS = 8
+# algorithmic bytes per ray (reads + writes of the data a phase must touch)
+BYTES_KEY = 32 + 8
+BYTES_SORT = 8 + (KEY_BITS // RADIX_BITS) * 2 * (8 + 4) - 4   # 196 for 64-bit keys, 8-bit digits
+BYTES_GATHER = 4 + 36 + 36
+BYTES_TRACE = 32 + 16
+BYTES_ACCUM = 32 + 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--bounce", type=int, default=3)
+    ap.add_argument("--small", action="store_true", help="tiny scene and wavefront (for profiling runs)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the per-bounce and e2e sweeps")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.p = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.out = open(os.devnull if False else "/tmp/rr_clocks_%d.csv" % os.getpid(), "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        if self.out is not None:
+            self.out.close()
+
+    def summary(self):
+        path = "/tmp/rr_clocks_%d.csv" % os.getpid()
+        try:
+            rows = [r.split(",") for r in open(path).read().strip().splitlines() if r.strip()]
+            os.remove(path)
+        except OSError:
+            rows = []
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if len(r) > 8]
+        mx = [float(r[2]) for r in rows if len(r) > 8]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) > 8:
+                for k, name in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workload(small: bool, seed: int):
+    from paper_2506_11273_gb300 import workloads as W
+    if small:
+        tris = W.scene_terrain(seed=seed, cells_x=128, cells_z=256, n_boxes=1000)
+        cam = W.Camera(width=480, height=270)
+    else:
+        tris = W.scene_terrain(seed=seed)
+        cam = W.Camera()
+    return tris, cam
+
+
+# ----------------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_11273_gb300 import rr
+    from paper_2506_11273_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    t0 = time.time()
+    tris, cam = build_workload(args.small, seed=2)
+    lo, hi = W.scene_aabb(tris)
+    bvh = rr.BVH(tris)
+    info = bvh.info()
+    table = rr.LengthTable(lo, hi)
+
+    # wavefronts of the path tracer, traced in natural (pixel) order; the
+    # adaptive table learns from every traced bounce, as the paper's does
+    fronts = []
+    rays = W.camera_rays(cam, seed=2 + 1000 * rank)
+    for b in range(1, 5):
+        fronts.append(rays)
+        o, d, _ = rr.to_device_rays(rays, dev)
+        h = torch.empty(len(rays), 4, device=dev)
+        rr.rr_trace(bvh, o, d, h)
+        if b < args.bounce:
+            table.accumulate(o, d, h)
+        hn = h.cpu().numpy()
+        if b < 4:
+            rays = W.next_bounce(tris, rays, hn, b, seed=2 + 1000 * rank)
+    setup_s = time.time() - t0
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def bounce_buffers(rays):
+        n = len(rays)
+        o, d, p = rr.to_device_rays(rays, dev)
+        bufs = dict(o=o, d=d, p=p, n=n,
+                    keys=torch.empty(n, dtype=torch.int64, device=dev),
+                    perm=torch.empty(n, dtype=torch.int32, device=dev),
+                    ws=rr.sort_workspace(n, KEY_BITS, RADIX_BITS, dev),
+                    so=torch.empty_like(o), sd=torch.empty_like(d), sp=torch.empty_like(p),
+                    hits=torch.empty(n, 4, device=dev))
+        return bufs
+
+    params_tp = rr.key_params(rr.RR_KEY_TWO_POINT, KEY_BITS, lo, hi, t_source=rr.RR_T_ADAPTIVE, table=table)
+    params_aila = rr.key_params(rr.RR_KEY_AILA, KEY_BITS, lo, hi)
+
+    def make_step(B, params, accumulate):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+
+        def step():
+            ev[0].record(stream)
+            rr.rr_compute_keys(B["o"], B["d"], params, B["keys"])
+            ev[1].record(stream)
+            rr.rr_sort(B["keys"], None, B["perm"], B["n"], KEY_BITS, RADIX_BITS, B["ws"])
+            ev[2].record(stream)
+            rr.rr_permute(B["o"], B["d"], B["p"], B["perm"], B["so"], B["sd"], B["sp"])
+            ev[3].record(stream)
+            rr.rr_trace(bvh, B["so"], B["sd"], B["hits"])
+            ev[4].record(stream)
+            if accumulate:
+                rr.rr_length_table_accumulate(table, B["so"], B["sd"], B["hits"])
+            ev[5].record(stream)
+
+        def phases():
+            return [ev[i].elapsed_time(ev[i + 1]) for i in range(5)]
+        return step, phases
+
+    def make_unsorted(B):
+        def step():
+            rr.rr_trace(bvh, B["o"], B["d"], B["hits"])
+        return step
+
+    def timed(step, K, W_, phases=None):
+        for _ in range(W_):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ph = []
+        total = 0.0
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        for k in range(K):
+            flush.zero_()
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+            if phases is not None:
+                torch.cuda.synchronize()
+                ph.append(phases())
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        times = [starts[k].elapsed_time(ends[k]) for k in range(K)]
+        total = float(sum(times))
+        return total, times, ph
+
+    head = fronts[args.bounce - 1]
+    B = bounce_buffers(head)
+    n = B["n"]
+    step_tp, phases_tp = make_step(B, params_tp, True)
+    l0 = rr.rr_kernel_launch_count()
+    with ClockSampler(local) as clk:
+        total_ms, times, ph = timed(step_tp, args.steps, args.warmup, phases_tp)
+    launches = (rr.rr_kernel_launch_count() - l0)
+    launches_timed = launches * args.steps // (args.steps + args.warmup)
+    clocks = clk.summary()
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * n * args.steps / (total_ms * 1e-3) / 1e6
+    ph = np.array(ph)
+    phase_ms = dict(zip(["key", "sort", "gather", "trace", "accum"], [float(x) for x in np.median(ph, axis=0)]))
+    if rr.rr_device_error() != 0:
+        raise RuntimeError("device error flag set during the bench")
+
+    extra = {}
+    # unsorted trace of the same rays, same conditions
+    tot_u, _, _ = timed(make_unsorted(B), args.steps, args.warmup)
+    unsorted = n * args.steps / (tot_u * 1e-3) / 1e6
+    # the origin-direction (Aila) key on the same rays
+    step_aila, phases_aila = make_step(B, params_aila, False)
+    tot_a, _, ph_a = timed(step_aila, max(3, args.steps // 2), 3, phases_aila)
+    aila = n * max(3, args.steps // 2) / (tot_a * 1e-3) / 1e6
+    extra["aila_mrays"] = round(aila, 2)
+    extra["aila_trace_ms"] = float(np.median(np.array(ph_a)[:, 3]))
+
+    if not args.no_extra:
+        per_bounce = []
+        for b, fr in enumerate(fronts, start=1):
+            Bb = bounce_buffers(fr)
+            st, pf = make_step(Bb, params_tp, False)
+            k = 5
+            tot_s, _, phb = timed(st, k, 3, pf)
+            tot_uu, _, _ = timed(make_unsorted(Bb), k, 3)
+            phb = np.median(np.array(phb), axis=0)
+            per_bounce.append({"bounce": b, "rays": Bb["n"],
+                               "sorted_e2e_mrays": round(Bb["n"] * k / (tot_s * 1e-3) / 1e6, 1),
+                               "unsorted_trace_mrays": round(Bb["n"] * k / (tot_uu * 1e-3) / 1e6, 1),
+                               "sorted_trace_mrays": round(Bb["n"] / (phb[3] * 1e-3) / 1e6, 1)})
+            del Bb
+        extra["per_bounce"] = per_bounce
+
+    # end to end through the C ABI with pinned host buffers
+    pipe = rr.Pipeline(bvh, n, params_tp, RADIX_BITS)
+    ho = torch.from_numpy(head.o_tmin).pin_memory()
+    hd = torch.from_numpy(head.d_tmax).pin_memory()
+    hp = torch.from_numpy(head.payload.view(np.int32)).pin_memory()
+    hh = torch.empty(n, 4, dtype=torch.float32).pin_memory()
+    hpo = torch.empty(n, dtype=torch.int32).pin_memory()
+    for _ in range(3):
+        pipe.run_host(ho, hd, hp, hh, hpo)
+    torch.cuda.synchronize()
+    ke = max(3, args.steps // 2)
+    t_e = []
+    for _ in range(ke):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        pipe.run_host(ho, hd, hp, hh, hpo)
+        t_e.append(time.perf_counter() - t1)
+    e2e = world * n / float(np.mean(t_e)) / 1e6
+    pipe.close()
+
+    hbm, peak_kind = peaks()
+    trace_ach = BYTES_TRACE * n / (phase_ms["trace"] * 1e-3) / 1e9
+    sort_ach = BYTES_SORT * n / (phase_ms["sort"] * 1e-3) / 1e9
+    gather_ach = BYTES_GATHER * n / (phase_ms["gather"] * 1e-3) / 1e9
+    key_ach = BYTES_KEY * n / (phase_ms["key"] * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64",
+        "data": "synthetic",
+        "config": {"workload": ("path tracer 1920x1080 1spp, bounce-%d wavefront, %d-triangle terrain; "
+                                "Two Point key (adaptive estimate) %d bits, radix %d" %
+                                (args.bounce, info.n_tris, KEY_BITS, RADIX_BITS)) if not args.small
+                   else "small profiling case",
+                   "rays_per_step": n, "triangles": int(info.n_tris), "bounce": args.bounce,
+                   "key": "two_point_adaptive", "key_bits": KEY_BITS, "radix_bits": RADIX_BITS,
+                   "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 gpu"},
+        "unsorted_mrays": round(unsorted, 2),
+        "speedup_vs_unsorted": round(value / unsorted, 3),
+        "phases_ms": {k: round(v, 4) for k, v in phase_ms.items()},
+        "roofline": {"bound": "hbm", "kernel": "trace", "achieved": round(trace_ach, 1), "peak": hbm,
+                     "unit": "GB/s", "frac": round(trace_ach / hbm, 4), "traffic": None,
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_ray": BYTES_TRACE},
+        "phase_roofline": {
+            "key": {"gbs": round(key_ach, 1), "frac": round(key_ach / hbm, 3), "bytes_per_ray": BYTES_KEY},
+            "sort": {"gbs": round(sort_ach, 1), "frac": round(sort_ach / hbm, 3), "bytes_per_ray": BYTES_SORT,
+                     "mkeys_s": round(n / (phase_ms["sort"] * 1e-3) / 1e6, 1)},
+            "gather": {"gbs": round(gather_ach, 1), "frac": round(gather_ach / hbm, 3), "bytes_per_ray": BYTES_GATHER},
+        },
+        "e2e": {"value": round(e2e, 2), "unit": UNIT, "h2d_bytes_per_step": 36 * n,
+                "d2h_bytes_per_step": 20 * n},
+        "gpu_launches": int(launches_timed),
+        "clocks": clocks,
+        "bvh": {"nodes": int(info.n_nodes), "depth": int(info.depth), "build_s": round(info.build_seconds, 2),
+                "bytes": int(info.node_bytes + info.tri_bytes)},
+        "setup_s": round(setup_s, 1),
+    }
+    out.update(extra)
+    if rank == 0:
+        out["cpu_baseline"] = cpu_baseline(tris, lo, hi, sample=20000 if args.small else 100000)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- oracle
+
+def oracle_bounce_time(tris, lo, hi, rays, obvh, table):
+    import oracle
+    t0 = time.perf_counter()
+    keys = oracle.compute_keys(oracle.TWO_POINT, KEY_BITS, rays.o_tmin, rays.d_tmax, lo, hi,
+                               tsrc=oracle.T_ADAPTIVE, table=table)
+    perm, _ = oracle.stable_sort(keys)
+    so, sd, sp = oracle.permute(rays.o_tmin, rays.d_tmax, rays.payload, perm)
+    h, _ = obvh.trace(so, sd)
+    table.accumulate(lo, hi, so, sd, h)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(tris, lo, hi, sample: int):
+    """The oracle (single thread) on a bounded sample of the same scene: a
+    trace-free stand-in secondary wavefront of `sample` rays."""
+    import oracle
+    from paper_2506_11273_gb300 import workloads as W
+    rays = W.surface_rays(tris, sample, seed=77)
+    obvh = oracle.BVH(tris)
+    table = oracle.LengthTable(oracle.largest_extent(lo, hi))
+    dt = oracle_bounce_time(tris, lo, hi, rays, obvh, table)
+    return {"value": round(sample / dt / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d stand-in secondary rays (origins on the scene by area, BSDF directions) of the "
+                      "same scene; keys+sort+gather+trace (oracle BVH)+accumulate, one thread" % sample,
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2506_11273_gb300 import workloads as W
+    import oracle
+    tris, _ = build_workload(args.small, seed=2)
+    lo, hi = W.scene_aabb(tris)
+    obvh = oracle.BVH(tris)
+    table = oracle.LengthTable(oracle.largest_extent(lo, hi))
+    sample = 5000 if args.small else 20000
+    rays = W.surface_rays(tris, sample, seed=77)
+    for _ in range(args.warmup):
+        oracle_bounce_time(tris, lo, hi, rays, obvh, table)
+    ts = [oracle_bounce_time(tris, lo, hi, rays, obvh, table) for _ in range(args.steps)]
+    value = sample * args.steps / sum(ts) / 1e6
+    desc = ("%d stand-in secondary rays per step (same scene), oracle keys+sort+gather+trace+accumulate, "
+            "one thread" % sample)
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(ts) / args.steps, 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64",
+           "data": "synthetic",
+           "config": {"workload": "path tracer 1920x1080 1spp scene, %d-ray sample per step" % sample,
+                      "key": "two_point_adaptive", "key_bits": KEY_BITS},
+           "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+           "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

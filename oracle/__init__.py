@@ -78,6 +78,9 @@ def lib():
             L.or_ray_triangle.restype = C.c_int
             L.or_ray_triangle.argtypes = [_f64p, _f64p, _f32p, C.POINTER(C.c_double),
                                           C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            L.or_ray_triangle_uv.restype = C.c_int
+            L.or_ray_triangle_uv.argtypes = [_f64p, _f64p, _f32p, C.POINTER(C.c_double),
+                                             C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.or_trace_brute.argtypes = [_f32p, C.c_uint32, _f32p, _f32p, C.c_uint32, _f32p,
                                          C.c_void_p]
             L.or_bvh_build.restype = C.c_void_p
@@ -207,6 +210,15 @@ def ray_triangle(o, d, tri):
     t, u, v = C.c_double(), C.c_double(), C.c_double()
     ok = lib().or_ray_triangle(np.ascontiguousarray(o, np.float64), np.ascontiguousarray(d, np.float64),
                                _f32(tri, 9), C.byref(t), C.byref(u), C.byref(v))
+    return (bool(ok), t.value, u.value, v.value)
+
+
+def ray_plane_barycentrics(o, d, tri):
+    """(ok, t, u, v) of the ray's meeting point with the triangle's plane (no inside test)."""
+    t, u, v = C.c_double(), C.c_double(), C.c_double()
+    ok = lib().or_ray_triangle_uv(np.ascontiguousarray(o, np.float64),
+                                  np.ascontiguousarray(d, np.float64), _f32(tri, 9), C.byref(t),
+                                  C.byref(u), C.byref(v))
     return (bool(ok), t.value, u.value, v.value)
 
 

@@ -370,6 +370,38 @@ int or_ray_triangle(const double o[3], const double d[3], const float *tri, doub
     return 1;
 }
 
+/*
+ * The same quantities without the inside test: barycentrics (u, v) and t of the
+ * ray's meeting point with the triangle's plane.  Returns 0 for a zero
+ * determinant.  Used by the tests to tell how close a ray passes to an edge.
+ */
+int or_ray_triangle_uv(const double o[3], const double d[3], const float *tri, double *t_out,
+                       double *u_out, double *v_out)
+{
+    double v0[3], e1[3], e2[3], pv[3], tv[3], qv[3];
+    for (int c = 0; c < 3; ++c) {
+        v0[c] = tri[c];
+        e1[c] = (double)tri[3 + c] - v0[c];
+        e2[c] = (double)tri[6 + c] - v0[c];
+    }
+    pv[0] = d[1] * e2[2] - d[2] * e2[1];
+    pv[1] = d[2] * e2[0] - d[0] * e2[2];
+    pv[2] = d[0] * e2[1] - d[1] * e2[0];
+    double det = e1[0] * pv[0] + e1[1] * pv[1] + e1[2] * pv[2];
+    if (det == 0.0)
+        return 0;
+    double inv = 1.0 / det;
+    for (int c = 0; c < 3; ++c)
+        tv[c] = o[c] - v0[c];
+    qv[0] = tv[1] * e1[2] - tv[2] * e1[1];
+    qv[1] = tv[2] * e1[0] - tv[0] * e1[2];
+    qv[2] = tv[0] * e1[1] - tv[1] * e1[0];
+    *u_out = (tv[0] * pv[0] + tv[1] * pv[1] + tv[2] * pv[2]) * inv;
+    *v_out = (d[0] * qv[0] + d[1] * qv[1] + d[2] * qv[2]) * inv;
+    *t_out = (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) * inv;
+    return 1;
+}
+
 static void or_write_hit(float *hits, double *info, uint32_t i, uint32_t tri, double t, double u,
                          double v)
 {

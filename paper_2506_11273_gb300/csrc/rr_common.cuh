@@ -66,8 +66,8 @@ struct rr_length_table {
 
 // Compressed 8-wide BVH node (80 bytes, five 16-byte loads).
 //   A child box is p + q * 2^(e - 127) per axis: q in [qlo, qhi] (8 bits each).
-//   meta[slot]: 0 = empty; bit 7 set = inner child, node index child_base + (meta & 7);
-//   otherwise a leaf of ((meta >> 5) & 3) + 1 triangles starting at
+//   meta[slot]: 0 = empty; meta >> 5 == 7: inner child, node index child_base + (meta & 7);
+//   otherwise a leaf of (meta >> 5) triangles (1..4) starting at
 //   tri_base + (meta & 31) in the BVH-ordered triangle array.
 struct alignas(16) RRNode8 {
     float px, py, pz;
@@ -96,6 +96,7 @@ struct rr_bvh {
     int device;
     RRNode8 *nodes;   // device
     RRTri *tris;      // device
+    float4 *planes;   // device, two per triangle (normal as hi + lo floats)
     uint32_t n_nodes;
     uint32_t n_tris;
     uint32_t root_is_leaf;  // scenes of 1..4 triangles: no inner node, the root is one leaf

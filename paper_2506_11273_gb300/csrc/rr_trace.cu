@@ -1,0 +1,339 @@
+// Closest-hit traversal of the compressed 8-wide BVH.
+//
+// Persistent warps take batches of consecutive rays from a global queue, so
+// which rays share a warp is decided by the order of the ray buffer: the
+// coherence that reordering is meant to create (Section 4.2 measures its
+// effect on control-flow and cache efficiency).  Each thread keeps a stack of
+// (node or leaf reference, entry distance) pairs; children are pushed farthest
+// first in the order given by the ray's direction octant, so the nearest
+// child is popped next, and popped entries that start beyond the closest hit
+// so far are culled.  Triangles are intersected with Moller-Trumbore in fp32.
+#include <chrono>
+#include <cmath>
+
+#include "rr_common.cuh"
+#include "rr_trace.h"
+
+namespace rr {
+
+constexpr int kTraceBlock = 128;
+constexpr uint32_t kQueueBatch = 64;  // rays per queue fetch (two rounds of 32 per warp)
+constexpr uint32_t kLeafFlag = 0x80000000u;
+
+struct TraceArgs {
+    const float4 *nodes;  // RRNode8 as five float4
+    const float4 *tris;   // RRTri as three float4
+    const float4 *planes; // two float4 per triangle: normal hi.xyz, lo.x | lo.y, lo.z
+    const float4 *o_tmin;
+    const float4 *d_tmax;
+    float4 *hits;
+    uint32_t n;
+    uint32_t n_nodes;
+    uint32_t *queue;  // [0] next ray, [1] finished blocks
+    uint32_t *err;
+};
+
+template <int S>
+__device__ __forceinline__ uint32_t slot_byte(uint32_t lo4, uint32_t hi4) {
+    return ((S < 4 ? lo4 : hi4) >> (8 * (S & 3))) & 0xFFu;
+}
+
+__device__ __forceinline__ float safe_inv(float x) {
+    const float m = fabsf(x) > 1e-18f ? x : copysignf(1e-18f, x);
+    return __frcp_rn(m);
+}
+
+// Error-free transformations (Knuth's TwoSum, FMA-based TwoProd).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// Distance along the ray to the plane of BVH-ordered triangle k, evaluated in
+// compensated fp32: t = ((v0 - o) . n) / (d . n) with n the triangle normal
+// stored as hi + lo floats and v0 - o split exactly into hi + lo.  Plain fp32
+// loses relative accuracy when the hit is close to the origin compared with
+// |v0 - o|; this form keeps it at a few ulps.
+__device__ __forceinline__ float refine_t(const TraceArgs &a, uint32_t k, float4 o, float4 d) {
+    const float4 v0 = __ldg(a.tris + 3 * (size_t)k);
+    const float4 p0 = __ldg(a.planes + 2 * (size_t)k), p1 = __ldg(a.planes + 2 * (size_t)k + 1);
+    const float nh[3] = {p0.x, p0.y, p0.z}, nl[3] = {p0.w, p1.x, p1.y};
+    const float vo[3] = {v0.x, v0.y, v0.z}, oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+    float num_hi = 0.0f, num_lo = 0.0f, den_hi = 0.0f, den_lo = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float w, wl, p, pe, s, se;
+        two_sum(vo[c], -oo[c], w, wl);  // v0 - o exactly
+        two_prod(w, nh[c], p, pe);
+        two_sum(num_hi, p, s, se);
+        num_hi = s;
+        num_lo = __fadd_rn(num_lo, __fadd_rn(__fadd_rn(se, pe), __fmaf_rn(w, nl[c], __fmul_rn(wl, nh[c]))));
+        two_prod(dd[c], nh[c], p, pe);
+        two_sum(den_hi, p, s, se);
+        den_hi = s;
+        den_lo = __fadd_rn(den_lo, __fadd_rn(__fadd_rn(se, pe), __fmul_rn(dd[c], nl[c])));
+    }
+    return __fdiv_rn(__fadd_rn(num_hi, num_lo), __fadd_rn(den_hi, den_lo));
+}
+
+__device__ __forceinline__ float4 trace_ray(const TraceArgs &a, float4 o, float4 d) {
+    const float tmin = o.w;
+    float best = d.w;
+    float bu = 0.0f, bv = 0.0f;
+    uint32_t best_tri = kMiss, best_k = 0;
+    const float idx = safe_inv(d.x), idy = safe_inv(d.y), idz = safe_inv(d.z);
+    const uint32_t negmask = (idx < 0.0f ? 1u : 0u) | (idy < 0.0f ? 2u : 0u) | (idz < 0.0f ? 4u : 0u);
+    uint2 stack[kTraceStack];
+    int sp = 0;
+    if (a.n_nodes > 0 && tmin <= best) stack[sp++] = make_uint2(0u, __float_as_uint(tmin));
+    while (sp > 0) {
+        const uint2 e = stack[--sp];
+        if (__uint_as_float(e.y) >= best) continue;
+        if (e.x & kLeafFlag) {
+            const uint32_t start = e.x & 0x0FFFFFFFu;
+            const uint32_t cnt = ((e.x >> 28) & 7u) + 1u;
+            for (uint32_t k = 0; k < cnt; ++k) {
+                const float4 *tp = a.tris + 3 * (size_t)(start + k);
+                const float4 v0 = __ldg(tp), e1 = __ldg(tp + 1), e2 = __ldg(tp + 2);
+                const float pvx = d.y * e2.z - d.z * e2.y;
+                const float pvy = d.z * e2.x - d.x * e2.z;
+                const float pvz = d.x * e2.y - d.y * e2.x;
+                const float det = e1.x * pvx + e1.y * pvy + e1.z * pvz;
+                if (det == 0.0f) continue;
+                const float inv = __frcp_rn(det);
+                const float tvx = o.x - v0.x, tvy = o.y - v0.y, tvz = o.z - v0.z;
+                const float u = (tvx * pvx + tvy * pvy + tvz * pvz) * inv;
+                if (!(u >= 0.0f && u <= 1.0f)) continue;
+                const float qvx = tvy * e1.z - tvz * e1.y;
+                const float qvy = tvz * e1.x - tvx * e1.z;
+                const float qvz = tvx * e1.y - tvy * e1.x;
+                const float v = (d.x * qvx + d.y * qvy + d.z * qvz) * inv;
+                if (!(v >= 0.0f && u + v <= 1.0f)) continue;
+                const float t = (e2.x * qvx + e2.y * qvy + e2.z * qvz) * inv;
+                if (t > tmin && t < best) {
+                    best = t;
+                    bu = u;
+                    bv = v;
+                    best_tri = __float_as_uint(v0.w);
+                    best_k = start + k;
+                }
+            }
+            continue;
+        }
+        const float4 *np = a.nodes + 5 * (size_t)e.x;
+        const float4 f0 = __ldg(np), f1 = __ldg(np + 1), f2 = __ldg(np + 2), f3 = __ldg(np + 3),
+                     f4 = __ldg(np + 4);
+        const uint32_t ew = __float_as_uint(f0.w);
+        const float sx = __uint_as_float((ew & 0xFFu) << 23);
+        const float sy = __uint_as_float(((ew >> 8) & 0xFFu) << 23);
+        const float sz = __uint_as_float(((ew >> 16) & 0xFFu) << 23);
+        const float ax = (f0.x - o.x) * idx, ay = (f0.y - o.y) * idy, az = (f0.z - o.z) * idz;
+        const float bx = sx * idx, by = sy * idy, bz = sz * idz;
+        const uint32_t child_base = __float_as_uint(f1.x), tri_base = __float_as_uint(f1.y);
+        const uint32_t meta_lo = __float_as_uint(f1.z), meta_hi = __float_as_uint(f1.w);
+        uint32_t nxl = __float_as_uint(f2.x), nxh = __float_as_uint(f2.y);
+        uint32_t nyl = __float_as_uint(f2.z), nyh = __float_as_uint(f2.w);
+        uint32_t nzl = __float_as_uint(f3.x), nzh = __float_as_uint(f3.y);
+        uint32_t fxl = __float_as_uint(f3.z), fxh = __float_as_uint(f3.w);
+        uint32_t fyl = __float_as_uint(f4.x), fyh = __float_as_uint(f4.y);
+        uint32_t fzl = __float_as_uint(f4.z), fzh = __float_as_uint(f4.w);
+        // for a negative direction the near plane is the box's high side
+        if (negmask & 1u) {
+            uint32_t t0 = nxl, t1 = nxh;
+            nxl = fxl; nxh = fxh; fxl = t0; fxh = t1;
+        }
+        if (negmask & 2u) {
+            uint32_t t0 = nyl, t1 = nyh;
+            nyl = fyl; nyh = fyh; fyl = t0; fyh = t1;
+        }
+        if (negmask & 4u) {
+            uint32_t t0 = nzl, t1 = nzh;
+            nzl = fzl; nzh = fzh; fzl = t0; fzh = t1;
+        }
+        float tn[8];
+        uint32_t hm = 0;
+#define RR_SLOT(S)                                                                                        \
+    {                                                                                                     \
+        const float tnx = fmaf((float)slot_byte<S>(nxl, nxh), bx, ax);                                    \
+        const float tny = fmaf((float)slot_byte<S>(nyl, nyh), by, ay);                                    \
+        const float tnz = fmaf((float)slot_byte<S>(nzl, nzh), bz, az);                                    \
+        const float tfx = fmaf((float)slot_byte<S>(fxl, fxh), bx, ax);                                    \
+        const float tfy = fmaf((float)slot_byte<S>(fyl, fyh), by, ay);                                    \
+        const float tfz = fmaf((float)slot_byte<S>(fzl, fzh), bz, az);                                    \
+        const float t0 = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, tmin));                                         \
+        const float t1 = fminf(fminf(tfx, tfy), fminf(tfz, best));                                          \
+        tn[S] = t0;                                                                                       \
+        if (slot_byte<S>(meta_lo, meta_hi) != 0u && t0 <= t1) hm |= 1u << (S ^ negmask);                  \
+    }
+        RR_SLOT(0) RR_SLOT(1) RR_SLOT(2) RR_SLOT(3) RR_SLOT(4) RR_SLOT(5) RR_SLOT(6) RR_SLOT(7)
+#undef RR_SLOT
+        const int cnt = __popc(hm);
+        if (sp + cnt > (int)kTraceStack) {
+            atomicOr(a.err, RR_DEVERR_TRACE_STACK);
+            best_tri = kMiss;
+            best = __int_as_float(0x7f800000);
+            break;
+        }
+#define RR_PUSH(S)                                                                                        \
+    {                                                                                                     \
+        const uint32_t pos = S ^ negmask;                                                                 \
+        if ((hm >> pos) & 1u) {                                                                           \
+            const uint32_t meta = slot_byte<S>(meta_lo, meta_hi);                                         \
+            const uint32_t ref = meta >= 0xE0u                                                            \
+                                     ? child_base + (meta & 7u)                                           \
+                                     : (kLeafFlag | (((meta >> 5) - 1u) << 28) | (tri_base + (meta & 31u))); \
+            stack[sp + __popc(hm >> (pos + 1))] = make_uint2(ref, __float_as_uint(tn[S]));                \
+        }                                                                                                 \
+    }
+        RR_PUSH(0) RR_PUSH(1) RR_PUSH(2) RR_PUSH(3) RR_PUSH(4) RR_PUSH(5) RR_PUSH(6) RR_PUSH(7)
+#undef RR_PUSH
+        sp += cnt;
+    }
+    if (best_tri == kMiss) return make_float4(__int_as_float(0x7f800000), 0.0f, 0.0f, __uint_as_float(kMiss));
+    const float tr = refine_t(a, best_k, o, d);
+    return make_float4(isfinite(tr) ? tr : best, bu, bv, __uint_as_float(best_tri));
+}
+
+__global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceArgs a) {
+    const uint32_t lane = threadIdx.x & 31u;
+    while (true) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(a.queue, kQueueBatch);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (base >= a.n) break;
+#pragma unroll 1
+        for (uint32_t r = 0; r < kQueueBatch; r += 32) {
+            const uint32_t i = base + r + lane;
+            if (i < a.n) a.hits[i] = trace_ray(a, __ldg(a.o_tmin + i), __ldg(a.d_tmax + i));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t prev = atomicAdd(a.queue + 1, 1u);
+        if (prev == gridDim.x - 1) {  // every block has stopped fetching: reset for the next launch
+            a.queue[0] = 0u;
+            a.queue[1] = 0u;
+        }
+    }
+}
+
+}  // namespace rr
+
+using namespace rr;
+
+extern "C" rr_status rr_build_bvh(const float *tris_host, uint32_t n_tris, rr_bvh **out) {
+    if (!out) return fail(RR_ERR_INVALID_ARG, "rr_build_bvh: out is NULL");
+    *out = nullptr;
+    if (n_tris > 0 && !tris_host) return fail(RR_ERR_INVALID_ARG, "rr_build_bvh: tris is NULL");
+    if (n_tris >= (1u << 28)) return fail(RR_ERR_UNSUPPORTED, "rr_build_bvh: at most 2^28 - 1 triangles");
+    rr_status st;
+    if (!device_state(&st)) return st;
+    const auto t0 = std::chrono::steady_clock::now();
+    HostBVH h;
+    std::string err;
+    st = build_wide_bvh(tris_host, n_tris, &h, &err);
+    if (st != RR_OK) return fail(st, err);
+    if (h.stack_need > kTraceStack)
+        return fail(RR_ERR_UNSUPPORTED, "rr_build_bvh: tree needs a deeper traversal stack than the kernel has");
+    rr_bvh *b = new rr_bvh();
+    cudaGetDevice(&b->device);
+    b->nodes = nullptr;
+    b->tris = nullptr;
+    b->planes = nullptr;
+    b->n_nodes = (uint32_t)h.nodes.size();
+    b->n_tris = n_tris;
+    b->root_is_leaf = 0;
+    b->root_leaf_ref = 0;
+    cudaError_t e = cudaSuccess;
+    if (b->n_nodes) {
+        e = cudaMalloc(&b->nodes, sizeof(RRNode8) * h.nodes.size());
+        if (e == cudaSuccess) e = cudaMalloc(&b->tris, sizeof(RRTri) * h.tris.size());
+        if (e == cudaSuccess) e = cudaMalloc(&b->planes, sizeof(float4) * h.planes.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->planes, h.planes.data(), sizeof(float4) * h.planes.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->nodes, h.nodes.data(), sizeof(RRNode8) * h.nodes.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->tris, h.tris.data(), sizeof(RRTri) * h.tris.size(), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(b->nodes);
+        cudaFree(b->tris);
+        cudaFree(b->planes);
+        delete b;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? RR_ERR_OOM : RR_ERR_CUDA, "rr_build_bvh: upload failed");
+    }
+    rr_bvh_info &i = b->info;
+    i.n_tris = n_tris;
+    i.n_nodes = b->n_nodes;
+    i.n_leaves = h.n_leaves;
+    i.depth = h.depth;
+    i.node_bytes = sizeof(RRNode8) * (uint64_t)h.nodes.size();
+    i.tri_bytes = sizeof(RRTri) * (uint64_t)h.tris.size() + sizeof(float4) * (uint64_t)h.planes.size();
+    for (int c = 0; c < 3; ++c) {
+        i.aabb_lo[c] = h.lo[c];
+        i.aabb_hi[c] = h.hi[c];
+    }
+    i.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = b;
+    return RR_OK;
+}
+
+extern "C" rr_status rr_bvh_destroy(rr_bvh *b) {
+    if (!b) return RR_OK;
+    cudaFree(b->nodes);
+    cudaFree(b->tris);
+    cudaFree(b->planes);
+    delete b;
+    return RR_OK;
+}
+
+extern "C" rr_status rr_bvh_get_info(const rr_bvh *b, rr_bvh_info *info) {
+    if (!b || !info) return fail(RR_ERR_INVALID_ARG, "rr_bvh_get_info: NULL argument");
+    *info = b->info;
+    return RR_OK;
+}
+
+extern "C" rr_status rr_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax, uint32_t n, float *hits_out,
+                              void *stream) {
+    if (!b) return fail(RR_ERR_INVALID_ARG, "rr_trace: NULL bvh");
+    if (n == 0) return RR_OK;
+    if (!o_tmin || !d_tmax || !hits_out) return fail(RR_ERR_INVALID_ARG, "rr_trace: NULL buffer");
+    if (!aligned16(o_tmin) || !aligned16(d_tmax) || !aligned16(hits_out))
+        return fail(RR_ERR_INVALID_ARG, "rr_trace: buffers not 16-byte aligned");
+    if (overlaps(hits_out, 16ull * n, o_tmin, 16ull * n) || overlaps(hits_out, 16ull * n, d_tmax, 16ull * n))
+        return fail(RR_ERR_INVALID_ARG, "rr_trace: hits overlap the rays");
+    rr_status st;
+    DeviceState *ds = device_state(&st);
+    if (!ds) return st;
+    static int blocks_per_sm = 0;
+    if (blocks_per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, trace_kernel, kTraceBlock, 0);
+        if (e != cudaSuccess || blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    const uint32_t slot = ds->next_counter.fetch_add(1) % (kCounterPool / 2);
+    TraceArgs a;
+    a.nodes = reinterpret_cast<const float4 *>(b->nodes);
+    a.tris = reinterpret_cast<const float4 *>(b->tris);
+    a.planes = b->planes;
+    a.o_tmin = reinterpret_cast<const float4 *>(o_tmin);
+    a.d_tmax = reinterpret_cast<const float4 *>(d_tmax);
+    a.hits = reinterpret_cast<float4 *>(hits_out);
+    a.n = n;
+    a.n_nodes = b->n_nodes;
+    a.queue = ds->counters + 2 * slot;
+    a.err = ds->err;
+    const uint32_t want = (n + kQueueBatch - 1) / kQueueBatch;  // warps that can get work
+    uint32_t grid = (uint32_t)ds->sm_count * (uint32_t)blocks_per_sm;
+    grid = std::max(1u, std::min(grid, (want + kTraceBlock / 32 - 1) / (kTraceBlock / 32)));
+    trace_kernel<<<grid, kTraceBlock, 0, as_stream(stream)>>>(a);
+    note_launches(1);
+    return check_launch("rr_trace");
+}

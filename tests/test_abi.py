@@ -1,0 +1,68 @@
+"""The C-ABI library builds, loads and exports every symbol include/rr.h
+declares (CPU only: no compute call is made)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rr.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(rr_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def librr():
+    from paper_2506_11273_gb300 import build
+    path = build.build()
+    return path
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("rr_compute_keys", "rr_sort", "rr_permute", "rr_trace", "rr_build_bvh"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(librr):
+    lib = ctypes.CDLL(librr)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", librr], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (rr_[a-z_0-9]+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_binding_lists_every_declared_symbol(librr):
+    from paper_2506_11273_gb300 import rr
+    assert sorted(rr.EXPORTS) == declared_functions()
+    rr.lib()  # argtypes resolve against the library
+
+
+def test_status_strings_without_a_gpu(librr):
+    from paper_2506_11273_gb300 import rr
+    assert rr.rr_status_string(0) == "ok"
+    assert rr.rr_status_string(1) == "invalid argument"
+    assert rr.rr_status_string(4) == "device wait timed out"
+
+
+def test_build_targets_sm_103a_only():
+    from paper_2506_11273_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_product_path_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2506_11273_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                text = open(os.path.join(dirpath, f), errors="replace").read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), f
+                assert "liboracle" not in text and "oracle.c" not in text, f

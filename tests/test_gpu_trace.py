@@ -1,0 +1,242 @@
+"""GPU parity: BVH build + closest-hit trace, and the one-bounce pipeline.
+
+Hits are compared with the oracle's binary64 closest hits under the rule in
+hitcheck.py (same triangle, t within 1e-5 relative; ties and edge-grazing
+rays classified).  The oracle BVH used for the larger scenes is itself pinned
+to the brute-force definition in the CPU tests.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2506_11273_gb300 import rr
+from paper_2506_11273_gb300 import workloads as W
+
+from hitcheck import compare
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_trace(bvh, rays):
+    o, d, _ = rr.to_device_rays(rays)
+    hits = torch.empty(len(rays), 4, dtype=torch.float32, device="cuda")
+    rr.rr_trace(bvh, o, d, hits)
+    torch.cuda.synchronize()
+    return hits.cpu().numpy()
+
+
+def check(tris, rays, brute=False, or_bvh=None, max_ambiguous=None):
+    bvh = rr.BVH(tris)
+    g = gpu_trace(bvh, rays)
+    if brute:
+        h, info = oracle.trace_brute(tris, rays.o_tmin, rays.d_tmax)
+    else:
+        h, info = (or_bvh or oracle.BVH(tris)).trace(rays.o_tmin, rays.d_tmax)
+    res = compare(tris, rays.o_tmin, rays.d_tmax, g, h, info, max_ambiguous=max_ambiguous)
+    assert rr.rr_device_error() == 0
+    return res, g, h
+
+
+def test_closed_form_box_interior():
+    tris = W._box_tris(np.zeros(3), np.ones(3), inward=True).astype(np.float32)
+    rays = W.random_rays_in_box(5000, [0.01] * 3, [0.99] * 3, seed=3)
+    res, g, _ = check(tris, rays, brute=True)
+    assert res["hit_rate"] == 1.0
+    o = rays.o_tmin[:, :3].astype(np.float64)
+    d = rays.d_tmax[:, :3].astype(np.float64)
+    with np.errstate(divide="ignore"):
+        tc = np.where(d != 0, (np.where(d > 0, 1.0, 0.0) - o) / d, np.inf)
+    assert np.allclose(g[:, 0], tc.min(axis=1), rtol=1e-5, atol=0)
+
+
+@pytest.mark.parametrize("n_tris", [0, 1, 2, 3, 4, 5, 8, 9, 33, 100])
+def test_tiny_scenes_brute_force(n_tris):
+    rng = np.random.default_rng(n_tris)
+    tris = (rng.random((n_tris, 9)) * 2 - 0.5).astype(np.float32)
+    rays = W.random_rays_in_box(4096, [-1] * 3, [2] * 3, seed=n_tris + 100)
+    check(tris, rays, brute=True)
+
+
+def test_box_soup_small_brute_force():
+    tris = W.scene_box_soup(seed=4, n_random=512)
+    rays = W.rays_box_soup(tris, n=8192, seed=4)
+    res, _, _ = check(tris, rays, brute=True)
+    assert res["hit_rate"] > 0.99
+
+
+def test_interval_ends_and_degenerate_rays():
+    tris = W.scene_box_soup(seed=5, n_random=256)
+    rays = W.rays_box_soup(tris, n=4096, seed=5)
+    o = rays.o_tmin.copy()
+    d = rays.d_tmax.copy()
+    o[:512, 3] = 0.3          # larger tmin
+    d[512:1024, 3] = 0.05     # short tmax
+    d[1024:1100, :3] = 0.0    # zero direction: no hit
+    d[1100:1200, 0] = 0.0     # axis-parallel directions
+    d[1200:1300, 1] = 0.0
+    o[1300:1400, 3] = 5.0     # tmin > tmax: empty interval
+    d[1300:1400, 3] = 1.0
+    r = W.Rays(o, d, rays.payload)
+    # axis-parallel rays that start on a wall of the unit box run inside the
+    # wall's plane: coplanar, hence grazing/edge cases by construction
+    res, _, _ = check(tris, r, brute=True, max_ambiguous=16)
+    assert res["definite"] == 0
+
+
+def test_degenerate_triangles_never_hit():
+    tris = np.array([[0, 0, 0, 1, 1, 1, 2, 2, 2],        # collinear
+                     [0.5, 0.5, 0.5, 0.5, 0.5, 0.5, 0.5, 0.5, 0.5],  # a point
+                     [0, 0, 0, 1, 0, 0, 0, 1, 0]], np.float32)
+    rays = W.random_rays_in_box(4096, [-1] * 3, [2] * 3, seed=7)
+    _, g, _ = check(tris, rays, brute=True)
+    tri = g[:, 3].view(np.uint32)
+    assert np.all((tri == 2) | (tri == rr.MISS))
+
+
+def test_config1_full_65536_rays():
+    tris = W.scene_box_soup(seed=1)
+    rays = W.rays_box_soup(tris, n=65536, seed=1)
+    res, _, _ = check(tris, rays)
+    assert res["hit_rate"] > 0.99
+
+
+def test_trace_is_order_agnostic_and_deterministic():
+    """The hit of each ray does not depend on where the ray sits in the buffer."""
+    tris = W.scene_box_soup(seed=1)
+    rays = W.rays_box_soup(tris, n=65536, seed=2)
+    bvh = rr.BVH(tris)
+    g1 = gpu_trace(bvh, rays)
+    g2 = gpu_trace(bvh, rays)
+    assert np.array_equal(g1.view(np.uint32), g2.view(np.uint32))
+    p = np.random.default_rng(1).permutation(len(rays))
+    g3 = gpu_trace(bvh, rays.subset(p))
+    assert np.array_equal(g3.view(np.uint32), g1[p].view(np.uint32))
+
+
+def test_bvh_info_and_box():
+    tris = W.scene_box_soup(seed=1)
+    bvh = rr.BVH(tris)
+    i = bvh.info()
+    lo, hi = W.scene_aabb(tris)
+    assert i.n_tris == tris.shape[0]
+    assert list(i.aabb_lo) == list(lo) and list(i.aabb_hi) == list(hi)
+    assert i.n_nodes > 0 and i.depth >= 2 and i.node_bytes == 80 * i.n_nodes
+    with pytest.raises(rr.RRError):
+        rr.BVH(np.array([[0, 0, 0, 1, np.nan, 0, 0, 1, 0]], np.float32))
+
+
+@pytest.fixture(scope="module")
+def terrain():
+    tris = W.scene_terrain()
+    return tris, rr.BVH(tris), oracle.BVH(tris)
+
+
+def test_config2_full_size_sampled(terrain):
+    """Full 1,168,576-triangle scene and full 2,073,600-ray wavefronts traced
+    in one launch; 20,000 sampled rays compared with the oracle."""
+    tris, bvh, obvh = terrain
+    info = bvh.info()
+    assert info.n_tris == tris.shape[0]
+    rng = np.random.default_rng(11)
+    for rays in (W.camera_rays(W.Camera()), W.surface_rays(tris, 2073600, seed=12)):
+        g = gpu_trace(bvh, rays)
+        idx = np.sort(rng.choice(len(rays), 20000, replace=False))
+        sub = rays.subset(idx)
+        h, inf = obvh.trace(sub.o_tmin, sub.d_tmax)
+        compare(tris, sub.o_tmin, sub.d_tmax, g[idx], h, inf)
+    assert rr.rr_device_error() == 0
+
+
+def test_config2_secondary_rays_from_oracle_hits(terrain):
+    """A path-tracer bounce built from oracle hits (no CUDA input): 50,000 rays."""
+    tris, bvh, obvh = terrain
+    cam = W.camera_rays(W.Camera()).subset(np.arange(0, 2073600, 41)[:50000])
+    h1, _ = obvh.trace(cam.o_tmin, cam.d_tmax)
+    sec = W.next_bounce(tris, cam, h1, 1, seed=2)
+    g = gpu_trace(bvh, sec)
+    h, inf = obvh.trace(sec.o_tmin, sec.d_tmax)
+    res = compare(tris, sec.o_tmin, sec.d_tmax, g, h, inf)
+    assert res["hit_rate"] > 0.5
+
+
+# ------------------------------------------------------------------ one bounce
+
+def oracle_bounce(tris, rays, lo, hi, layout, bits, tsrc, table=None, obvh=None):
+    keys = oracle.compute_keys(layout, bits, rays.o_tmin, rays.d_tmax, lo, hi, tsrc=tsrc, table=table)
+    perm, _ = oracle.stable_sort(keys)
+    o, d, p = oracle.permute(rays.o_tmin, rays.d_tmax, rays.payload, perm)
+    h, info = (obvh or oracle.BVH(tris)).trace(o, d)
+    if table is not None:
+        table.accumulate(lo, hi, o, d, h)
+    return keys, perm, o, d, p, h, info
+
+
+def check_table_close(table, otable, ambiguous):
+    """The GPU table accumulates the GPU's fp32 hit distances and the oracle's
+    table its binary64 ones, so cells agree to the trace tolerance: counts
+    exactly (up to edge-ambiguous rays), sums within 1e-5 relative plus one
+    fixed-point unit per ray."""
+    s, c = table.read()
+    dc = c.astype(np.int64) - otable.cnt.astype(np.int64)
+    assert np.abs(dc).sum() <= ambiguous
+    same = dc == 0
+    added = otable.sum[same].astype(np.float64) - 4194304.0
+    bound = 1e-5 * added + (otable.cnt[same].astype(np.float64) - 1.0) + 1.0
+    diff = np.abs(s[same].astype(np.float64) - otable.sum[same].astype(np.float64))
+    assert np.all(diff <= bound)
+
+
+@pytest.mark.parametrize("name,layout,olayout,bits,tsrc,otsrc", [
+    ("aila32", rr.RR_KEY_AILA, oracle.AILA, 32, rr.RR_T_FIXED, oracle.T_FIXED),
+    ("tp64_fixed", rr.RR_KEY_TWO_POINT, oracle.TWO_POINT, 64, rr.RR_T_FIXED, oracle.T_FIXED),
+    ("tp64_adaptive", rr.RR_KEY_TWO_POINT, oracle.TWO_POINT, 64, rr.RR_T_ADAPTIVE, oracle.T_ADAPTIVE),
+])
+def test_pipeline_matches_oracle_config1(name, layout, olayout, bits, tsrc, otsrc):
+    tris = W.scene_box_soup(seed=1)
+    rays = W.rays_box_soup(tris, n=65536, seed=3)
+    lo, hi = W.scene_aabb(tris)
+    E = oracle.largest_extent(lo, hi)
+    obvh = oracle.BVH(tris)
+    bvh = rr.BVH(tris)
+    adaptive = tsrc == rr.RR_T_ADAPTIVE
+    table = rr.LengthTable(lo, hi) if adaptive else None
+    params = rr.key_params(layout, bits, lo, hi, t_source=tsrc, table=table)
+    pipe = rr.Pipeline(bvh, len(rays), params, radix_bits=8)
+    o, d, p = rr.to_device_rays(rays)
+    hits = torch.empty(len(rays), 4, device="cuda")
+    pout = torch.empty_like(p)
+    for entry in ("device", "host"):
+        if adaptive:
+            table.reset()
+        otable = oracle.LengthTable(E) if adaptive else None
+        if entry == "device":
+            pipe.run(o, d, p, hits, pout)
+            torch.cuda.synchronize()
+            gh, gp = hits.cpu().numpy(), rr.u32_to_numpy(pout)
+        else:
+            gh = np.zeros((len(rays), 4), np.float32)
+            gp = np.zeros(len(rays), np.uint32)
+            pipe.run_host(rays.o_tmin, rays.d_tmax, rays.payload, gh, gp)
+        keys, perm, so, sd, sp, h, info = oracle_bounce(tris, rays, lo, hi, olayout, bits, otsrc, otable, obvh)
+        assert np.array_equal(gp, sp)  # payload order == oracle permutation
+        res = compare(tris, so, sd, gh, h, info)
+        if adaptive:
+            check_table_close(table, otable, res["ambiguous"])
+    assert rr.rr_device_error() == 0
+    pipe.close()
+
+
+def test_pipeline_rejects_bad_arguments():
+    tris = W.scene_box_soup(seed=1, n_random=64)
+    lo, hi = W.scene_aabb(tris)
+    bvh = rr.BVH(tris)
+    params = rr.key_params(rr.RR_KEY_AILA, 32, lo, hi)
+    pipe = rr.Pipeline(bvh, 100, params)
+    rays = W.rays_box_soup(tris, n=200, seed=1)
+    o, d, p = rr.to_device_rays(rays)
+    hits = torch.empty(200, 4, device="cuda")
+    with pytest.raises(rr.RRError):
+        pipe.run(o, d, p, hits, torch.empty_like(p))  # n > max_n
+    with pytest.raises(rr.RRError):
+        rr.Pipeline(bvh, 100, params, radix_bits=6)
