@@ -50,7 +50,8 @@ typedef enum {
     RR_ERR_OOM = 3,         /* a library-owned allocation failed */
     RR_ERR_TIMEOUT = 4,     /* device: a bounded wait gave up (radix-sort look-back) */
     RR_ERR_STACK = 5,       /* device: a traversal stack would have overflowed */
-    RR_ERR_UNSUPPORTED = 6  /* a valid request this build does not handle */
+    RR_ERR_UNSUPPORTED = 6, /* a valid request this build does not handle */
+    RR_ERR_TOO_LARGE = 7    /* n exceeds the fixed maximum of rr_sort_noalloc */
 } rr_status;
 
 /* Device error flags accumulated in the per-device error word. */
@@ -132,7 +133,7 @@ rr_status rr_sort_workspace_size(uint32_t n, uint32_t bits, uint32_t radix_bits,
 
 /*
  * rr_sort - stable least-significant-digit radix sort of (key, index) pairs
- * (Section 3.2: "the sorting is performed on key-index pairs first").
+ * (Section 3.2: the pairs are sorted first and the ray data moved afterwards).
  *
  * perm_out[i] = index of the i-th smallest key; equal keys keep their input
  * order.  keys_in (device, uint32 for bits <= 32 else uint64) is not modified;
@@ -146,6 +147,40 @@ rr_status rr_sort_workspace_size(uint32_t n, uint32_t bits, uint32_t radix_bits,
 rr_status rr_sort(const void *keys_in, void *keys_out, uint32_t *perm_out, uint32_t n,
                   uint32_t bits, uint32_t radix_bits, void *workspace, size_t workspace_bytes,
                   void *stream);
+
+/*
+ * rr_sort_noalloc - rr_sort for callers that cannot allocate device memory.
+ * The paper has no counterpart: it exists for integration, not for the method.
+ *
+ * Some callers cannot give rr_sort a workspace: a renderer or game engine whose
+ * own allocator owns the device-memory budget, a plug-in running inside such a
+ * host, or a real-time frame loop that forbids cudaMalloc/cudaFree once it has
+ * started.  This entry point allocates nothing.  Its scratch is one file-scope
+ * device array of RR_SORT_NOALLOC_SCRATCH_BYTES (24 MiB) inside librr.so, and
+ * every GPU that loads the library holds that array until the process exits.
+ *
+ * Arguments and results are those of rr_sort without the workspace: perm_out
+ * receives the stable order, keys_out (may be NULL) the sorted keys.  n may be
+ * at most RR_SORT_NOALLOC_MAX_N (2^20 keys); a larger n returns
+ * RR_ERR_TOO_LARGE and enqueues nothing.  Other bad arguments return
+ * RR_ERR_INVALID_ARG.  Errors are reported by the returned status only; this
+ * call records no message for rr_last_error_message().
+ *
+ * The first call on a device does a one-time set-up with that device current:
+ * it looks up the array's device address (cudaGetSymbolAddress) and the SM
+ * count.  Make that first call before any stream capture.
+ *
+ * All calls on a device share the one array, and the array keeps the last
+ * call's contents; each call clears what must start at zero before it uses it.
+ * Calls whose work can overlap on the GPU (on different streams, or from host
+ * threads without ordering between them) race on the array: serialise them.
+ * The per-call error word lives in the array and is cleared by each call, so a
+ * look-back timeout is not visible through rr_device_error().
+ */
+#define RR_SORT_NOALLOC_MAX_N (1u << 20)
+#define RR_SORT_NOALLOC_SCRATCH_BYTES (24u << 20)
+rr_status rr_sort_noalloc(const void *keys_in, void *keys_out, uint32_t *perm_out, uint32_t n,
+                          uint32_t bits, uint32_t radix_bits, void *stream);
 
 /* ---------------------------------------------------------------- reorder */
 

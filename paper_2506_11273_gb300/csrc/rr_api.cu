@@ -102,6 +102,7 @@ extern "C" const char *rr_status_string(rr_status s) {
         case RR_ERR_TIMEOUT: return "device wait timed out";
         case RR_ERR_STACK: return "traversal stack overflow";
         case RR_ERR_UNSUPPORTED: return "unsupported";
+        case RR_ERR_TOO_LARGE: return "size exceeds the fixed maximum of the no-allocation entry point";
     }
     return "unknown status";
 }

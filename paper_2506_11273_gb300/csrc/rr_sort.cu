@@ -5,6 +5,7 @@
 // decoupled look-back over the preceding tiles, and scatters through shared
 // memory so that global writes come out in runs.
 #include <algorithm>
+#include <mutex>
 
 #include "rr_common.cuh"
 
@@ -370,4 +371,165 @@ extern "C" rr_status rr_sort(const void *keys_in, void *keys_out, uint32_t *perm
     return radix_bits == 8
                ? run_sort<unsigned long long, 8>(pl, ki, ko, perm_out, n, bits, ws, ds->err, ds->sm_count, s)
                : run_sort<unsigned long long, 4>(pl, ki, ko, perm_out, n, bits, ws, ds->err, ds->sm_count, s);
+}
+
+// ------------------------------------------------------------------ sort without allocation
+//
+// rr_sort_noalloc: the same sort with its scratch in a file-scope device array
+// instead of a caller-supplied workspace, for callers that cannot allocate
+// device memory when they sort.  Nothing here allocates: not the array (it is
+// part of the loaded module), not the per-device set-up, not the launches.
+
+namespace rr {
+
+constexpr size_t cx_align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Mirror of plan_sort's total for the largest cases (constant expression).
+constexpr size_t cx_sort_bytes(uint32_t n, uint32_t bits, uint32_t rbits, uint32_t items) {
+    const size_t passes = (bits + rbits - 1) / rbits, radix = (size_t)1 << rbits, kb = bits > 32 ? 8 : 4;
+    const size_t tiles = (n + (size_t)kSortBlock * items - 1) / ((size_t)kSortBlock * items);
+    size_t off = cx_align256(4 * passes * radix);
+    off = cx_align256(off + 4 * passes);
+    off = cx_align256(off + 4 * passes * tiles * radix);
+    off = cx_align256(off + kb * n);
+    off = cx_align256(off + kb * n);
+    off = cx_align256(off + 4 * (size_t)n);
+    return off;
+}
+constexpr size_t cx_max(size_t a, size_t b) { return a > b ? a : b; }
+
+constexpr size_t kNoAllocHeader = 256;  // device error word of this entry point
+constexpr size_t kNoAllocScratchBytes =
+    kNoAllocHeader +
+    cx_max(cx_max(cx_sort_bytes(RR_SORT_NOALLOC_MAX_N, 64, 8, SortTile<unsigned long long>::kItems),
+                  cx_sort_bytes(RR_SORT_NOALLOC_MAX_N, 64, 4, SortTile<unsigned long long>::kItems)),
+           cx_max(cx_sort_bytes(RR_SORT_NOALLOC_MAX_N, 32, 8, SortTile<uint32_t>::kItems),
+                  cx_sort_bytes(RR_SORT_NOALLOC_MAX_N, 32, 4, SortTile<uint32_t>::kItems)));
+static_assert(kNoAllocScratchBytes <= RR_SORT_NOALLOC_SCRATCH_BYTES, "scratch bound in rr.h is too small");
+
+static __device__ __align__(256) unsigned char g_sort_scratch[RR_SORT_NOALLOC_SCRATCH_BYTES];
+
+struct NoAllocDevice {
+    unsigned char *scratch = nullptr;  // device address of g_sort_scratch on this device
+    int sm_count = 0;
+};
+constexpr int kNoAllocMaxDevices = 64;
+static NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+static std::mutex g_noalloc_mutex;
+
+// Per-device set-up, done by the first call on each device with that device
+// current: look up the array's device address (host code may not use the
+// symbol itself) and the SM count.
+static rr_status noalloc_device(NoAllocDevice **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RR_ERR_CUDA;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return RR_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    NoAllocDevice &d = g_noalloc_dev[dev];
+    if (d.scratch == nullptr) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return RR_ERR_CUDA;
+        }
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+            cudaGetLastError();
+            return RR_ERR_CUDA;
+        }
+        d.sm_count = sms;
+        d.scratch = static_cast<unsigned char *>(p);
+    }
+    *out = &d;
+    return RR_OK;
+}
+
+template <typename K, int RBITS>
+static rr_status launch_sort_noalloc(const SortPlan &pl, const K *keys_in, K *keys_out, uint32_t *perm_out,
+                                     uint32_t n, uint32_t bits, unsigned char *scratch, int sm_count,
+                                     cudaStream_t s) {
+    uint32_t *err = reinterpret_cast<uint32_t *>(scratch);
+    unsigned char *ws = scratch + kNoAllocHeader;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(ws + pl.off_hist);
+    uint32_t *counters = reinterpret_cast<uint32_t *>(ws + pl.off_counters);
+    uint32_t *lookback = reinterpret_cast<uint32_t *>(ws + pl.off_lookback);
+    K *keys_a = reinterpret_cast<K *>(ws + pl.off_keys_a);
+    K *keys_b = reinterpret_cast<K *>(ws + pl.off_keys_b);
+    uint32_t *vals_ws = reinterpret_cast<uint32_t *>(ws + pl.off_vals);
+    // the array keeps the last call's contents: clear the error word, the
+    // histograms and the tile counters (the look-back words are cleared by
+    // the histogram kernel)
+    if (cudaMemsetAsync(scratch, 0, kNoAllocHeader + pl.off_lookback, s) != cudaSuccess) {
+        cudaGetLastError();
+        return RR_ERR_CUDA;
+    }
+    const size_t zero_count = (size_t)pl.passes * pl.tiles * pl.radix / 4;
+    const uint32_t hist_blocks =
+        std::max(1u, std::min((n + kSortBlock - 1) / kSortBlock, (uint32_t)sm_count * 4u));
+    sort_histogram_kernel<K, RBITS><<<hist_blocks, kSortBlock, 0, s>>>(
+        keys_in, n, bits, pl.passes, hist, reinterpret_cast<uint4 *>(lookback), zero_count);
+    const size_t smem = pass_smem<K, RBITS>();
+    const K *kin = keys_in;
+    const uint32_t *vin = nullptr;
+    for (uint32_t p = 0; p < pl.passes; ++p) {
+        const bool final_slot = ((pl.passes - 1 - p) & 1u) == 0;
+        K *kout;
+        if (p == pl.passes - 1)
+            kout = keys_out;
+        else
+            kout = final_slot ? (keys_out ? keys_out : keys_b) : keys_a;
+        uint32_t *vout = final_slot ? perm_out : vals_ws;
+        PassArgs<K> a;
+        a.keys_in = kin;
+        a.vals_in = vin;
+        a.keys_out = kout;
+        a.vals_out = vout;
+        a.n = n;
+        a.shift = p * RBITS;
+        const uint32_t nb = std::min<uint32_t>(RBITS, bits - p * RBITS);
+        a.mask = (1u << nb) - 1u;
+        a.hist = hist + p * pl.radix;
+        a.lookback = lookback + (size_t)p * pl.tiles * pl.radix;
+        a.tile_counter = counters + p;
+        a.err = err;
+        onesweep_kernel<K, RBITS><<<pl.tiles, kSortBlock, smem, s>>>(a);
+        kin = kout;
+        vin = vout;
+    }
+    note_launches(1 + pl.passes);
+    if (cudaGetLastError() != cudaSuccess) return RR_ERR_CUDA;
+    return RR_OK;
+}
+
+}  // namespace rr
+
+extern "C" rr_status rr_sort_noalloc(const void *keys_in, void *keys_out, uint32_t *perm_out, uint32_t n,
+                                     uint32_t bits, uint32_t radix_bits, void *stream) {
+    if (bits < 1 || bits > 64 || (radix_bits != 4 && radix_bits != 8)) return RR_ERR_INVALID_ARG;
+    if (n > RR_SORT_NOALLOC_MAX_N) return RR_ERR_TOO_LARGE;
+    if (n == 0) return RR_OK;
+    if (!keys_in || !perm_out) return RR_ERR_INVALID_ARG;
+    const SortPlan pl = plan_sort(n, bits, radix_bits);
+    if (kNoAllocHeader + pl.total > sizeof(g_sort_scratch)) return RR_ERR_TOO_LARGE;
+    const size_t kbytes = (size_t)pl.kb * n;
+    if (!aligned(keys_in, pl.kb) || (keys_out && !aligned(keys_out, pl.kb)) || !aligned(perm_out, 4))
+        return RR_ERR_INVALID_ARG;
+    if (overlaps(keys_in, kbytes, perm_out, 4ull * n) ||
+        (keys_out && (overlaps(keys_out, kbytes, keys_in, kbytes) || overlaps(keys_out, kbytes, perm_out, 4ull * n))))
+        return RR_ERR_INVALID_ARG;
+    NoAllocDevice *d = nullptr;
+    const rr_status st = noalloc_device(&d);
+    if (st != RR_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    if (pl.kb == 4) {
+        const uint32_t *ki = static_cast<const uint32_t *>(keys_in);
+        uint32_t *ko = static_cast<uint32_t *>(keys_out);
+        return radix_bits == 8 ? launch_sort_noalloc<uint32_t, 8>(pl, ki, ko, perm_out, n, bits, d->scratch, d->sm_count, s)
+                               : launch_sort_noalloc<uint32_t, 4>(pl, ki, ko, perm_out, n, bits, d->scratch, d->sm_count, s);
+    }
+    const unsigned long long *ki = static_cast<const unsigned long long *>(keys_in);
+    unsigned long long *ko = static_cast<unsigned long long *>(keys_out);
+    return radix_bits == 8
+               ? launch_sort_noalloc<unsigned long long, 8>(pl, ki, ko, perm_out, n, bits, d->scratch, d->sm_count, s)
+               : launch_sort_noalloc<unsigned long long, 4>(pl, ki, ko, perm_out, n, bits, d->scratch, d->sm_count, s);
 }

@@ -33,7 +33,8 @@ MISS = 0xFFFFFFFF
 TABLE_CELLS = 1 << 20
 
 STATUS = {0: "RR_OK", 1: "RR_ERR_INVALID_ARG", 2: "RR_ERR_CUDA", 3: "RR_ERR_OOM",
-          4: "RR_ERR_TIMEOUT", 5: "RR_ERR_STACK", 6: "RR_ERR_UNSUPPORTED"}
+          4: "RR_ERR_TIMEOUT", 5: "RR_ERR_STACK", 6: "RR_ERR_UNSUPPORTED", 7: "RR_ERR_TOO_LARGE"}
+RR_SORT_NOALLOC_MAX_N = 1 << 20
 
 # every symbol include/rr.h declares
 EXPORTS = [
@@ -42,7 +43,7 @@ EXPORTS = [
     "rr_length_table_reset", "rr_length_table_accumulate", "rr_length_table_read",
     "rr_length_table_write", "rr_length_table_destroy", "rr_pipeline_create",
     "rr_pipeline_destroy", "rr_pipeline_run", "rr_pipeline_run_host", "rr_device_error",
-    "rr_status_string", "rr_last_error_message", "rr_kernel_launch_count",
+    "rr_status_string", "rr_last_error_message", "rr_kernel_launch_count", "rr_sort_noalloc",
 ]
 
 
@@ -77,6 +78,7 @@ def lib():
             L.rr_compute_keys.argtypes = [vp, vp, u32, C.POINTER(KeyParams), vp, vp]
             L.rr_sort_workspace_size.argtypes = [u32, u32, u32, C.POINTER(C.c_size_t)]
             L.rr_sort.argtypes = [vp, vp, vp, u32, u32, u32, vp, C.c_size_t, vp]
+            L.rr_sort_noalloc.argtypes = [vp, vp, vp, u32, u32, u32, vp]
             L.rr_permute.argtypes = [vp, vp, vp, vp, u32, vp, vp, vp, vp]
             L.rr_build_bvh.argtypes = [vp, u32, C.POINTER(vp)]
             L.rr_bvh_destroy.argtypes = [vp]
@@ -175,6 +177,15 @@ def rr_sort(keys_in, keys_out, perm_out, n: int, bits: int, radix_bits: int, wor
     nbytes = workspace.numel() * workspace.element_size()
     _check(lib().rr_sort(_ptr(keys_in), _ptr(keys_out), _ptr(perm_out), n, bits, radix_bits,
                          _ptr(workspace), nbytes, _stream(stream)), "rr_sort")
+
+
+def rr_sort_noalloc(keys_in, keys_out, perm_out, n: int, bits: int, radix_bits: int, stream=None):
+    """rr_sort without a workspace argument, for callers that cannot allocate device
+    memory (n <= RR_SORT_NOALLOC_MAX_N).  Errors come back as the status only."""
+    st = lib().rr_sort_noalloc(_ptr(keys_in), _ptr(keys_out), _ptr(perm_out), n, bits, radix_bits,
+                               _stream(stream))
+    if st != 0:
+        raise RRError(st, "rr_sort_noalloc", rr_status_string(st))
 
 
 def sort_workspace(n: int, bits: int, radix_bits: int = 8, device="cuda") -> torch.Tensor:
