@@ -156,7 +156,7 @@ rr_status rr_sort(const void *keys_in, void *keys_out, uint32_t *perm_out, uint3
  * own allocator owns the device-memory budget, a plug-in running inside such a
  * host, or a real-time frame loop that forbids cudaMalloc/cudaFree once it has
  * started.  This entry point allocates nothing.  Its scratch is one file-scope
- * device array of RR_SORT_NOALLOC_SCRATCH_BYTES (24 MiB) inside librr.so, and
+ * device array of RR_SORT_NOALLOC_SCRATCH_BYTES (26 MiB) inside librr.so, and
  * every GPU that loads the library holds that array until the process exits.
  *
  * Arguments and results are those of rr_sort without the workspace: perm_out
@@ -178,7 +178,7 @@ rr_status rr_sort(const void *keys_in, void *keys_out, uint32_t *perm_out, uint3
  * look-back timeout is not visible through rr_device_error().
  */
 #define RR_SORT_NOALLOC_MAX_N (1u << 20)
-#define RR_SORT_NOALLOC_SCRATCH_BYTES (24u << 20)
+#define RR_SORT_NOALLOC_SCRATCH_BYTES (26u << 20)
 rr_status rr_sort_noalloc(const void *keys_in, void *keys_out, uint32_t *perm_out, uint32_t n,
                           uint32_t bits, uint32_t radix_bits, void *stream);
 

@@ -213,9 +213,6 @@ rr_status build_wide_bvh(const float *tris, uint32_t n, HostBVH *out, std::strin
     std::deque<WideTask> q;
     out->nodes.emplace_back();
     q.push_back({root, 0u, 1u});
-    std::vector<uint32_t> stack_need;  // per wide node, filled bottom-up below
-    std::vector<std::vector<uint32_t>> wchildren;  // wide inner children per wide node
-    std::vector<uint32_t> wnchild;
     while (!q.empty()) {
         WideTask task = q.front();
         q.pop_front();
@@ -308,11 +305,17 @@ rr_status build_wide_bvh(const float *tris, uint32_t n, HostBVH *out, std::strin
             if (b.nodes[c].count == 0) ++n_inner;
         node.child_base = (uint32_t)out->nodes.size();
         node.tri_base = (uint32_t)out->tris.size();
+        // children in slot order: inner children get consecutive node indices in
+        // slot order (rank = inner children in lower slots), leaf triangles are
+        // appended in slot order
+        int child_in_slot[8];
+        for (int k = 0; k < 8; ++k) child_in_slot[k] = -1;
+        for (size_t i = 0; i < ch.size(); ++i) child_in_slot[slot_of[i]] = (int)i;
         uint32_t inner_rank = 0;
-        std::vector<uint32_t> inner_ids;
-        for (size_t i = 0; i < ch.size(); ++i) {
+        for (int s = 0; s < 8; ++s) {
+            if (child_in_slot[s] < 0) continue;
+            const size_t i = (size_t)child_in_slot[s];
             const BNode &cn = b.nodes[ch[i]];
-            const int s = slot_of[i];
             for (int c = 0; c < 3; ++c) {
                 const double step = std::ldexp(1.0, e[c]);
                 double ql = std::floor(((double)cn.box.lo[c] - p[c]) / step) - 1.0;
@@ -324,15 +327,14 @@ rr_status build_wide_bvh(const float *tris, uint32_t n, HostBVH *out, std::strin
                 qlo[c][s] = (uint8_t)ql;
                 qhi[c][s] = (uint8_t)qh;
             }
+            node.valid |= 1u << s;
             if (cn.count == 0) {
-                node.meta[s] = (uint8_t)(0xE0u | inner_rank);
+                node.imask |= (uint8_t)(1u << s);
                 const uint32_t wid = node.child_base + inner_rank;
-                inner_ids.push_back(wid);
                 q.push_back({ch[i], wid, task.depth + 1});
                 ++inner_rank;
             } else {
-                const uint32_t off = (uint32_t)out->tris.size() - node.tri_base;
-                node.meta[s] = (uint8_t)((cn.count << 5) | off);
+                node.tribits |= ((1u << cn.count) - 1u) << (4 * s);
                 for (uint32_t k = cn.first; k < cn.first + cn.count; ++k) {
                     const uint32_t t = b.order[k];
                     const float *v = &tris[9 * (size_t)t];
@@ -365,22 +367,9 @@ rr_status build_wide_bvh(const float *tris, uint32_t n, HostBVH *out, std::strin
         }
         for (uint32_t k = 0; k < n_inner; ++k) out->nodes.emplace_back();
         out->nodes[task.wnode] = node;
-        if (wchildren.size() <= task.wnode) {
-            wchildren.resize(task.wnode + 1);
-            wnchild.resize(task.wnode + 1);
-        }
-        wchildren[task.wnode] = inner_ids;
-        wnchild[task.wnode] = (uint32_t)ch.size();
     }
-    // worst-case traversal stack: S(node) = max(k, k - 1 + max over inner children S(c))
-    const size_t nw = out->nodes.size();
-    stack_need.assign(nw, 0);
-    for (size_t i = nw; i-- > 0;) {
-        uint32_t k = wnchild[i], m = 0;
-        for (uint32_t c : wchildren[i]) m = std::max(m, stack_need[c]);
-        stack_need[i] = std::max(k, k - 1 + m);
-    }
-    out->stack_need = stack_need[0];
+    // the traversal pushes at most one node group per level it descends
+    out->stack_need = out->depth;
     return RR_OK;
 }
 

@@ -65,16 +65,23 @@ struct rr_length_table {
 };
 
 // Compressed 8-wide BVH node (80 bytes, five 16-byte loads).
-//   A child box is p + q * 2^(e - 127) per axis: q in [qlo, qhi] (8 bits each).
-//   meta[slot]: 0 = empty; meta >> 5 == 7: inner child, node index child_base + (meta & 7);
-//   otherwise a leaf of (meta >> 5) triangles (1..4) starting at
-//   tri_base + (meta & 31) in the BVH-ordered triangle array.
+//   A child box is p + q * 2^(e - 127) per axis: q in [qlo, qhi] (8 bits each),
+//   widened by one step on every side of the child it bounds.
+//   imask: bit s set when slot s holds an inner child.  Inner children are
+//   stored consecutively in slot order: the child in slot s is node
+//   child_base + popc(imask & ((1 << s) - 1)).
+//   tribits: four bits per slot; leaf slot s holds `count` (1..4) triangles,
+//   marked by the low `count` bits of nibble s.  Leaf triangles are stored
+//   consecutively in slot order: the triangle of bit b is number
+//   tri_base + popc(tribits & ((1 << b) - 1)) of the BVH-ordered array.
+//   valid: bit s set when slot s is used (inner child or leaf).
 struct alignas(16) RRNode8 {
     float px, py, pz;
-    uint8_t ex, ey, ez, pad0;
+    uint8_t ex, ey, ez, imask;
     uint32_t child_base;
     uint32_t tri_base;
-    uint8_t meta[8];
+    uint32_t tribits;
+    uint32_t valid;
     uint8_t qlo_x[8];
     uint8_t qlo_y[8];
     uint8_t qlo_z[8];

@@ -1,9 +1,10 @@
 // Stable LSD radix sort of (key, index) pairs (Section 3.2), onesweep style:
-// one upfront pass builds the digit histograms of every pass; then each
-// digit pass is a single kernel in which a tile ranks its keys with warp
-// match_any, publishes its per-digit counts, resolves its global offsets by a
-// decoupled look-back over the preceding tiles, and scatters through shared
-// memory so that global writes come out in runs.
+// one upfront pass counts the digits of every pass; then each digit pass is a
+// single kernel in which a tile ranks its keys (peer masks from warp votes),
+// publishes its per-digit counts, resolves its global offsets by a
+// decoupled look-back over the preceding tiles (a window of predecessors read
+// at once), and scatters through shared memory so that global writes come out
+// in runs.
 #include <algorithm>
 #include <mutex>
 
@@ -17,6 +18,8 @@ constexpr uint32_t kValMask = (1u << 30) - 1u;
 constexpr uint32_t kSpinLimit = 1u << 20;   // bounded wait on a predecessor's word
 constexpr int kSortBlock = 256;
 constexpr int kSortWarps = kSortBlock / 32;
+constexpr uint32_t kHistMaxBlocks = 512;    // blocks of the counting pass
+constexpr int kLookbackWindow = 16;         // predecessor tiles read per look-back round
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
     uint32_t v;
@@ -48,6 +51,21 @@ __device__ __forceinline__ uint32_t digit_of(K k, uint32_t shift, uint32_t mask)
     return (uint32_t)(k >> shift) & mask;
 }
 
+// Lanes of `among` whose digit equals this lane's digit: one warp vote per
+// digit bit (votes are cheap; a match instruction per key is not).  Every lane
+// of the warp must call it; lanes outside `among` get an unspecified result.
+template <int RBITS>
+__device__ __forceinline__ uint32_t digit_peers(uint32_t dg, uint32_t among) {
+    uint32_t peers = among;
+#pragma unroll
+    for (int b = 0; b < RBITS; ++b) {
+        const uint32_t bit = (dg >> b) & 1u;
+        const uint32_t vote = __ballot_sync(0xFFFFFFFFu, bit);
+        peers &= bit ? vote : ~vote;
+    }
+    return peers;
+}
+
 // Exclusive scan of one value per thread over the first `RADIX` threads
 // (threads beyond contribute zero).  Called by every thread of the block.
 template <int RADIX>
@@ -77,26 +95,38 @@ __global__ void __launch_bounds__(kSortBlock) sort_histogram_kernel(const K *__r
                                                                    uint32_t bits, uint32_t passes,
                                                                    uint32_t *__restrict__ hist,
                                                                    uint4 *__restrict__ zero_words,
-                                                                   size_t zero_count) {
+                                                                   size_t zero_count, uint32_t *counters,
+                                                                   uint32_t *zero_err) {
     constexpr int RADIX = 1 << RBITS;
     constexpr int PMAX = (64 + RBITS - 1) / RBITS;
+    constexpr int KPT = 4;  // keys per lane per round
     __shared__ uint32_t sh[PMAX * RADIX];
     const uint32_t lane = threadIdx.x & 31u;
     for (uint32_t i = threadIdx.x; i < PMAX * RADIX; i += kSortBlock) sh[i] = 0;
+    if (blockIdx.x == 0) {
+        if (threadIdx.x < passes) counters[threadIdx.x] = 0u;  // tile counters of every pass
+        if (threadIdx.x == 0 && zero_err) *zero_err = 0u;
+    }
     __syncthreads();
-    const uint32_t stride = gridDim.x * kSortBlock;
-    for (uint32_t base = blockIdx.x * kSortBlock + (threadIdx.x & ~31u); base < n; base += stride) {
-        const uint32_t i = base + lane;
-        const bool valid = i < n;
-        const uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
-        if (valid) {
-            const K k = keys[i];
-            for (uint32_t p = 0; p < passes; ++p) {
-                const uint32_t shift = p * RBITS;
-                const uint32_t nb = min((uint32_t)RBITS, bits - shift);
-                const uint32_t dg = digit_of(k, shift, (1u << nb) - 1u);
-                const uint32_t peers = __match_any_sync(vmask, dg);
-                if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sh[p * RADIX + dg], __popc(peers));
+    const uint32_t stride = gridDim.x * kSortBlock * KPT;
+    for (uint32_t base = blockIdx.x * kSortBlock * KPT + (threadIdx.x & ~31u) * KPT; base < n; base += stride) {
+        K k[KPT];
+        uint32_t vmask[KPT];
+#pragma unroll
+        for (int q = 0; q < KPT; ++q) {
+            const uint32_t i = base + q * 32 + lane;
+            k[q] = i < n ? keys[i] : (K)0;
+            vmask[q] = __ballot_sync(0xFFFFFFFFu, i < n);
+        }
+        for (uint32_t p = 0; p < passes; ++p) {
+            const uint32_t shift = p * RBITS;
+            const uint32_t mask = (1u << min((uint32_t)RBITS, bits - shift)) - 1u;
+#pragma unroll
+            for (int q = 0; q < KPT; ++q) {
+                const uint32_t dg = digit_of(k[q], shift, mask);
+                const uint32_t peers = digit_peers<RBITS>(dg, vmask[q]);
+                if (((vmask[q] >> lane) & 1u) && lane == (uint32_t)(__ffs(peers) - 1))
+                    atomicAdd(&sh[p * RADIX + dg], __popc(peers));
             }
         }
     }
@@ -104,7 +134,7 @@ __global__ void __launch_bounds__(kSortBlock) sort_histogram_kernel(const K *__r
     for (uint32_t i = threadIdx.x; i < passes * RADIX; i += kSortBlock)
         if (sh[i]) atomicAdd(&hist[i], sh[i]);
     // the look-back words of every pass start at zero
-    for (size_t i = (size_t)blockIdx.x * kSortBlock + threadIdx.x; i < zero_count; i += stride)
+    for (size_t i = (size_t)blockIdx.x * kSortBlock + threadIdx.x; i < zero_count; i += (size_t)gridDim.x * kSortBlock)
         zero_words[i] = make_uint4(0u, 0u, 0u, 0u);
 }
 
@@ -126,7 +156,7 @@ struct PassArgs {
 };
 
 template <typename K, int RBITS>
-__global__ void __launch_bounds__(kSortBlock) onesweep_kernel(PassArgs<K> a) {
+__global__ void __launch_bounds__(kSortBlock, 3) onesweep_kernel(PassArgs<K> a) {
     constexpr int RADIX = 1 << RBITS;
     constexpr int ITEMS = SortTile<K>::kItems;
     constexpr int TILE = kSortBlock * ITEMS;
@@ -160,13 +190,19 @@ __global__ void __launch_bounds__(kSortBlock) onesweep_kernel(PassArgs<K> a) {
             v[j] = 0;
         }
     }
-    // stable rank inside the warp: items in index order (j, then lane)
+    // stable rank inside the warp: items in index order (j, then lane).  The
+    // peer masks of every row are independent; only the per-digit counters chain.
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const bool valid = wbase + j * 32 + lane < a.n;
-        const uint32_t dg = valid ? digit_of(k[j], a.shift, a.mask) : (uint32_t)RADIX;
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg);
+        r[j] = digit_peers<RBITS>(digit_of(k[j], a.shift, a.mask), __ballot_sync(0xFFFFFFFFu, valid));
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const bool valid = wbase + j * 32 + lane < a.n;
+        const uint32_t dg = digit_of(k[j], a.shift, a.mask);
+        const uint32_t peers = r[j];
         const uint32_t cur = valid ? s_wh[warp * RADIX + dg] : 0u;
         __syncwarp();
         if (valid && lane == 31u - __clz(peers)) s_wh[warp * RADIX + dg] = cur + __popc(peers);
@@ -187,25 +223,46 @@ __global__ void __launch_bounds__(kSortBlock) onesweep_kernel(PassArgs<K> a) {
     }
     const uint32_t dstart = scan_digits<RADIX>(tid < RADIX ? a.hist[tid] : 0u, s_misc + 8);
     const uint32_t lstart = scan_digits<RADIX>(cnt, s_misc + 8);
+    uint32_t excl = 0;
     if (tid < RADIX) {
-        uint32_t excl = 0;
         if (tile > 0) {
-            // decoupled look-back: add predecessors' counts until one holds a prefix
-            uint32_t j = tile - 1, spins = 0;
+            // decoupled look-back over a window of predecessors at a time: sum
+            // their counts from the nearest one back until a word holds a
+            // prefix; restart from a predecessor that has not published yet
+            int j = (int)tile - 1;
+            uint32_t spins = 0;
             while (true) {
-                const uint32_t w = ld_relaxed(a.lookback + (size_t)j * RADIX + tid);
-                const uint32_t fl = w & ~kValMask;
-                if (fl == 0u) {
-                    if (++spins > kSpinLimit) {
-                        atomicOr(a.err, RR_DEVERR_LOOKBACK_TIMEOUT);
-                        break;
+                uint32_t w[kLookbackWindow];
+#pragma unroll
+                for (int q = 0; q < kLookbackWindow; ++q)
+                    w[q] = (j - q >= 0) ? ld_relaxed(a.lookback + (size_t)(j - q) * RADIX + tid) : kFlagPrefix;
+                int status = 0, stop = 0;  // 0: keep going back, 1: prefix found, 2: not yet published
+                uint32_t add = 0;
+#pragma unroll
+                for (int q = 0; q < kLookbackWindow; ++q) {
+                    if (status == 0) {
+                        const uint32_t fl = w[q] & ~kValMask;
+                        if (fl == 0u) {
+                            status = 2;
+                            stop = q;
+                        } else {
+                            add += w[q] & kValMask;
+                            if (fl == kFlagPrefix) status = 1;
+                        }
                     }
-                    __nanosleep(32);
+                }
+                excl += add;
+                if (status == 1) break;
+                if (status == 0) {
+                    j -= kLookbackWindow;
                     continue;
                 }
-                excl += w & kValMask;
-                if (fl == kFlagPrefix || j == 0) break;
-                --j;
+                j -= stop;
+                if (++spins > kSpinLimit) {
+                    atomicOr(a.err, RR_DEVERR_LOOKBACK_TIMEOUT);
+                    break;
+                }
+                __nanosleep(32);
             }
             st_relaxed(a.lookback + (size_t)tile * RADIX + tid, kFlagPrefix | ((excl + cnt) & kValMask));
         }
@@ -236,15 +293,17 @@ __global__ void __launch_bounds__(kSortBlock) onesweep_kernel(PassArgs<K> a) {
 
 // ------------------------------------------------------------------ host side
 
-static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct SortPlan {
     uint32_t passes, radix, tiles, kb;
     size_t off_hist, off_counters, off_lookback, off_keys_a, off_keys_b, off_vals, total;
 };
 
-static SortPlan plan_sort(uint32_t n, uint32_t bits, uint32_t radix_bits) {
-    SortPlan p;
+// Workspace layout: digit counts [pass][radix], tile counters [pass],
+// look-back words [pass][tile][radix], two key buffers and one value buffer.
+constexpr SortPlan plan_sort(uint32_t n, uint32_t bits, uint32_t radix_bits) {
+    SortPlan p{};
     p.passes = (bits + radix_bits - 1) / radix_bits;
     p.radix = 1u << radix_bits;
     p.kb = bits > 32 ? 8u : 4u;
@@ -274,9 +333,13 @@ static size_t pass_smem() {
     return sizeof(K) * TILE + sizeof(uint32_t) * (TILE + kSortWarps * RADIX + 2 * RADIX + 16);
 }
 
+// Enqueues the whole sort: counting pass, one kernel per digit pass.
+// Allocates nothing.  zero_err (may be null) is a device word cleared
+// before the passes run.
 template <typename K, int RBITS>
-static rr_status run_sort(const SortPlan &pl, const K *keys_in, K *keys_out, uint32_t *perm_out, uint32_t n,
-                          uint32_t bits, unsigned char *ws, uint32_t *err, int sm_count, cudaStream_t s) {
+static cudaError_t enqueue_sort(const SortPlan &pl, const K *keys_in, K *keys_out, uint32_t *perm_out,
+                                uint32_t n, uint32_t bits, unsigned char *ws, uint32_t *err, uint32_t *zero_err,
+                                int sm_count, cudaStream_t s) {
     uint32_t *hist = reinterpret_cast<uint32_t *>(ws + pl.off_hist);
     uint32_t *counters = reinterpret_cast<uint32_t *>(ws + pl.off_counters);
     uint32_t *lookback = reinterpret_cast<uint32_t *>(ws + pl.off_lookback);
@@ -284,13 +347,14 @@ static rr_status run_sort(const SortPlan &pl, const K *keys_in, K *keys_out, uin
     K *keys_b = reinterpret_cast<K *>(ws + pl.off_keys_b);
     uint32_t *vals_ws = reinterpret_cast<uint32_t *>(ws + pl.off_vals);
 
-    cudaError_t e = cudaMemsetAsync(ws, 0, pl.off_lookback, s);
-    if (e != cudaSuccess) return fail_cuda(e, "rr_sort: memset");
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * pl.passes * pl.radix, s);
+    if (e != cudaSuccess) return e;
     const size_t zero_count = (size_t)pl.passes * pl.tiles * pl.radix / 4;
-    const uint32_t hist_blocks =
-        std::max(1u, std::min((n + kSortBlock - 1) / kSortBlock, (uint32_t)sm_count * 4u));
+    const uint32_t per_block = kSortBlock * 4u;
+    const uint32_t hist_blocks = std::max(
+        1u, std::min({(n + per_block - 1) / per_block, 2u * (uint32_t)sm_count, kHistMaxBlocks}));
     sort_histogram_kernel<K, RBITS><<<hist_blocks, kSortBlock, 0, s>>>(
-        keys_in, n, bits, pl.passes, hist, reinterpret_cast<uint4 *>(lookback), zero_count);
+        keys_in, n, bits, pl.passes, hist, reinterpret_cast<uint4 *>(lookback), zero_count, counters, zero_err);
     const size_t smem = pass_smem<K, RBITS>();
     const K *kin = keys_in;
     const uint32_t *vin = nullptr;
@@ -320,7 +384,16 @@ static rr_status run_sort(const SortPlan &pl, const K *keys_in, K *keys_out, uin
         vin = vout;
     }
     note_launches(1 + pl.passes);
-    return check_launch("rr_sort");
+    return cudaGetLastError();
+}
+
+template <typename K, int RBITS>
+static rr_status run_sort(const SortPlan &pl, const K *keys_in, K *keys_out, uint32_t *perm_out, uint32_t n,
+                          uint32_t bits, unsigned char *ws, uint32_t *err, int sm_count, cudaStream_t s) {
+    const cudaError_t e = enqueue_sort<K, RBITS>(pl, keys_in, keys_out, perm_out, n, bits, ws, err, nullptr,
+                                                 sm_count, s);
+    if (e != cudaSuccess) return fail_cuda(e, "rr_sort");
+    return RR_OK;
 }
 
 }  // namespace rr
@@ -382,29 +455,14 @@ extern "C" rr_status rr_sort(const void *keys_in, void *keys_out, uint32_t *perm
 
 namespace rr {
 
-constexpr size_t cx_align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-// Mirror of plan_sort's total for the largest cases (constant expression).
-constexpr size_t cx_sort_bytes(uint32_t n, uint32_t bits, uint32_t rbits, uint32_t items) {
-    const size_t passes = (bits + rbits - 1) / rbits, radix = (size_t)1 << rbits, kb = bits > 32 ? 8 : 4;
-    const size_t tiles = (n + (size_t)kSortBlock * items - 1) / ((size_t)kSortBlock * items);
-    size_t off = cx_align256(4 * passes * radix);
-    off = cx_align256(off + 4 * passes);
-    off = cx_align256(off + 4 * passes * tiles * radix);
-    off = cx_align256(off + kb * n);
-    off = cx_align256(off + kb * n);
-    off = cx_align256(off + 4 * (size_t)n);
-    return off;
-}
 constexpr size_t cx_max(size_t a, size_t b) { return a > b ? a : b; }
 
 constexpr size_t kNoAllocHeader = 256;  // device error word of this entry point
 constexpr size_t kNoAllocScratchBytes =
-    kNoAllocHeader +
-    cx_max(cx_max(cx_sort_bytes(RR_SORT_NOALLOC_MAX_N, 64, 8, SortTile<unsigned long long>::kItems),
-                  cx_sort_bytes(RR_SORT_NOALLOC_MAX_N, 64, 4, SortTile<unsigned long long>::kItems)),
-           cx_max(cx_sort_bytes(RR_SORT_NOALLOC_MAX_N, 32, 8, SortTile<uint32_t>::kItems),
-                  cx_sort_bytes(RR_SORT_NOALLOC_MAX_N, 32, 4, SortTile<uint32_t>::kItems)));
+    kNoAllocHeader + cx_max(cx_max(plan_sort(RR_SORT_NOALLOC_MAX_N, 64, 8).total,
+                                   plan_sort(RR_SORT_NOALLOC_MAX_N, 64, 4).total),
+                            cx_max(plan_sort(RR_SORT_NOALLOC_MAX_N, 32, 8).total,
+                                   plan_sort(RR_SORT_NOALLOC_MAX_N, 32, 4).total));
 static_assert(kNoAllocScratchBytes <= RR_SORT_NOALLOC_SCRATCH_BYTES, "scratch bound in rr.h is too small");
 
 static __device__ __align__(256) unsigned char g_sort_scratch[RR_SORT_NOALLOC_SCRATCH_BYTES];
@@ -448,57 +506,12 @@ template <typename K, int RBITS>
 static rr_status launch_sort_noalloc(const SortPlan &pl, const K *keys_in, K *keys_out, uint32_t *perm_out,
                                      uint32_t n, uint32_t bits, unsigned char *scratch, int sm_count,
                                      cudaStream_t s) {
+    // the array keeps the last call's contents: the counting kernel clears the
+    // error word, the tile counters and the look-back words before the passes
     uint32_t *err = reinterpret_cast<uint32_t *>(scratch);
-    unsigned char *ws = scratch + kNoAllocHeader;
-    uint32_t *hist = reinterpret_cast<uint32_t *>(ws + pl.off_hist);
-    uint32_t *counters = reinterpret_cast<uint32_t *>(ws + pl.off_counters);
-    uint32_t *lookback = reinterpret_cast<uint32_t *>(ws + pl.off_lookback);
-    K *keys_a = reinterpret_cast<K *>(ws + pl.off_keys_a);
-    K *keys_b = reinterpret_cast<K *>(ws + pl.off_keys_b);
-    uint32_t *vals_ws = reinterpret_cast<uint32_t *>(ws + pl.off_vals);
-    // the array keeps the last call's contents: clear the error word, the
-    // histograms and the tile counters (the look-back words are cleared by
-    // the histogram kernel)
-    if (cudaMemsetAsync(scratch, 0, kNoAllocHeader + pl.off_lookback, s) != cudaSuccess) {
-        cudaGetLastError();
-        return RR_ERR_CUDA;
-    }
-    const size_t zero_count = (size_t)pl.passes * pl.tiles * pl.radix / 4;
-    const uint32_t hist_blocks =
-        std::max(1u, std::min((n + kSortBlock - 1) / kSortBlock, (uint32_t)sm_count * 4u));
-    sort_histogram_kernel<K, RBITS><<<hist_blocks, kSortBlock, 0, s>>>(
-        keys_in, n, bits, pl.passes, hist, reinterpret_cast<uint4 *>(lookback), zero_count);
-    const size_t smem = pass_smem<K, RBITS>();
-    const K *kin = keys_in;
-    const uint32_t *vin = nullptr;
-    for (uint32_t p = 0; p < pl.passes; ++p) {
-        const bool final_slot = ((pl.passes - 1 - p) & 1u) == 0;
-        K *kout;
-        if (p == pl.passes - 1)
-            kout = keys_out;
-        else
-            kout = final_slot ? (keys_out ? keys_out : keys_b) : keys_a;
-        uint32_t *vout = final_slot ? perm_out : vals_ws;
-        PassArgs<K> a;
-        a.keys_in = kin;
-        a.vals_in = vin;
-        a.keys_out = kout;
-        a.vals_out = vout;
-        a.n = n;
-        a.shift = p * RBITS;
-        const uint32_t nb = std::min<uint32_t>(RBITS, bits - p * RBITS);
-        a.mask = (1u << nb) - 1u;
-        a.hist = hist + p * pl.radix;
-        a.lookback = lookback + (size_t)p * pl.tiles * pl.radix;
-        a.tile_counter = counters + p;
-        a.err = err;
-        onesweep_kernel<K, RBITS><<<pl.tiles, kSortBlock, smem, s>>>(a);
-        kin = kout;
-        vin = vout;
-    }
-    note_launches(1 + pl.passes);
-    if (cudaGetLastError() != cudaSuccess) return RR_ERR_CUDA;
-    return RR_OK;
+    const cudaError_t e = enqueue_sort<K, RBITS>(pl, keys_in, keys_out, perm_out, n, bits, scratch + kNoAllocHeader,
+                                                 err, err, sm_count, s);
+    return e == cudaSuccess ? RR_OK : RR_ERR_CUDA;
 }
 
 }  // namespace rr

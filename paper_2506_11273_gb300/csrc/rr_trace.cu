@@ -3,11 +3,12 @@
 // Persistent warps take batches of consecutive rays from a global queue, so
 // which rays share a warp is decided by the order of the ray buffer: the
 // coherence that reordering is meant to create (Section 4.2 measures its
-// effect on control-flow and cache efficiency).  Each thread keeps a stack of
-// (node or leaf reference, entry distance) pairs; children are pushed farthest
-// first in the order given by the ray's direction octant, so the nearest
-// child is popped next, and popped entries that start beyond the closest hit
-// so far are culled.  Triangles are intersected with Moller-Trumbore in fp32.
+// effect on control-flow and cache efficiency).  Each thread walks the
+// compressed 8-wide BVH with a stack of node groups (the hit children of a
+// node that remain to be visited, in the near-to-far order given by the ray's
+// direction octant); the leaves a node's children hit are tested at once.
+// Triangles are intersected with Moller-Trumbore in fp32 and the winning
+// distance is refined in compensated fp32.
 #include <chrono>
 #include <cmath>
 
@@ -16,9 +17,7 @@
 
 namespace rr {
 
-constexpr int kTraceBlock = 128;
-constexpr uint32_t kQueueBatch = 64;  // rays per queue fetch (two rounds of 32 per warp)
-constexpr uint32_t kLeafFlag = 0x80000000u;
+constexpr int kTraceBlock = 256;
 
 struct TraceArgs {
     const float4 *nodes;  // RRNode8 as five float4
@@ -32,11 +31,6 @@ struct TraceArgs {
     uint32_t *queue;  // [0] next ray, [1] finished blocks
     uint32_t *err;
 };
-
-template <int S>
-__device__ __forceinline__ uint32_t slot_byte(uint32_t lo4, uint32_t hi4) {
-    return ((S < 4 ? lo4 : hi4) >> (8 * (S & 3))) & 0xFFu;
-}
 
 __device__ __forceinline__ float safe_inv(float x) {
     const float m = fabsf(x) > 1e-18f ? x : copysignf(1e-18f, x);
@@ -81,135 +75,222 @@ __device__ __forceinline__ float refine_t(const TraceArgs &a, uint32_t k, float4
     return __fdiv_rn(__fadd_rn(num_hi, num_lo), __fadd_rn(den_hi, den_lo));
 }
 
-__device__ __forceinline__ float4 trace_ray(const TraceArgs &a, float4 o, float4 d) {
-    const float tmin = o.w;
-    float best = d.w;
-    float bu = 0.0f, bv = 0.0f;
-    uint32_t best_tri = kMiss, best_k = 0;
-    const float idx = safe_inv(d.x), idy = safe_inv(d.y), idz = safe_inv(d.z);
-    const uint32_t negmask = (idx < 0.0f ? 1u : 0u) | (idy < 0.0f ? 2u : 0u) | (idz < 0.0f ? 4u : 0u);
-    uint2 stack[kTraceStack];
-    int sp = 0;
-    if (a.n_nodes > 0 && tmin <= best) stack[sp++] = make_uint2(0u, __float_as_uint(tmin));
-    while (sp > 0) {
-        const uint2 e = stack[--sp];
-        if (__uint_as_float(e.y) >= best) continue;
-        if (e.x & kLeafFlag) {
-            const uint32_t start = e.x & 0x0FFFFFFFu;
-            const uint32_t cnt = ((e.x >> 28) & 7u) + 1u;
-            for (uint32_t k = 0; k < cnt; ++k) {
-                const float4 *tp = a.tris + 3 * (size_t)(start + k);
-                const float4 v0 = __ldg(tp), e1 = __ldg(tp + 1), e2 = __ldg(tp + 2);
-                const float pvx = d.y * e2.z - d.z * e2.y;
-                const float pvy = d.z * e2.x - d.x * e2.z;
-                const float pvz = d.x * e2.y - d.y * e2.x;
-                const float det = e1.x * pvx + e1.y * pvy + e1.z * pvz;
-                if (det == 0.0f) continue;
-                const float inv = __frcp_rn(det);
-                const float tvx = o.x - v0.x, tvy = o.y - v0.y, tvz = o.z - v0.z;
-                const float u = (tvx * pvx + tvy * pvy + tvz * pvz) * inv;
-                if (!(u >= 0.0f && u <= 1.0f)) continue;
-                const float qvx = tvy * e1.z - tvz * e1.y;
-                const float qvy = tvz * e1.x - tvx * e1.z;
-                const float qvz = tvx * e1.y - tvy * e1.x;
-                const float v = (d.x * qvx + d.y * qvy + d.z * qvz) * inv;
-                if (!(v >= 0.0f && u + v <= 1.0f)) continue;
-                const float t = (e2.x * qvx + e2.y * qvy + e2.z * qvz) * inv;
-                if (t > tmin && t < best) {
-                    best = t;
-                    bu = u;
-                    bv = v;
-                    best_tri = __float_as_uint(v0.w);
-                    best_k = start + k;
-                }
-            }
-            continue;
-        }
-        const float4 *np = a.nodes + 5 * (size_t)e.x;
-        const float4 f0 = __ldg(np), f1 = __ldg(np + 1), f2 = __ldg(np + 2), f3 = __ldg(np + 3),
-                     f4 = __ldg(np + 4);
-        const uint32_t ew = __float_as_uint(f0.w);
-        const float sx = __uint_as_float((ew & 0xFFu) << 23);
-        const float sy = __uint_as_float(((ew >> 8) & 0xFFu) << 23);
-        const float sz = __uint_as_float(((ew >> 16) & 0xFFu) << 23);
-        const float ax = (f0.x - o.x) * idx, ay = (f0.y - o.y) * idy, az = (f0.z - o.z) * idz;
-        const float bx = sx * idx, by = sy * idy, bz = sz * idz;
-        const uint32_t child_base = __float_as_uint(f1.x), tri_base = __float_as_uint(f1.y);
-        const uint32_t meta_lo = __float_as_uint(f1.z), meta_hi = __float_as_uint(f1.w);
-        uint32_t nxl = __float_as_uint(f2.x), nxh = __float_as_uint(f2.y);
-        uint32_t nyl = __float_as_uint(f2.z), nyh = __float_as_uint(f2.w);
-        uint32_t nzl = __float_as_uint(f3.x), nzh = __float_as_uint(f3.y);
-        uint32_t fxl = __float_as_uint(f3.z), fxh = __float_as_uint(f3.w);
-        uint32_t fyl = __float_as_uint(f4.x), fyh = __float_as_uint(f4.y);
-        uint32_t fzl = __float_as_uint(f4.z), fzh = __float_as_uint(f4.w);
-        // for a negative direction the near plane is the box's high side
-        if (negmask & 1u) {
-            uint32_t t0 = nxl, t1 = nxh;
-            nxl = fxl; nxh = fxh; fxl = t0; fxh = t1;
-        }
-        if (negmask & 2u) {
-            uint32_t t0 = nyl, t1 = nyh;
-            nyl = fyl; nyh = fyh; fyl = t0; fyh = t1;
-        }
-        if (negmask & 4u) {
-            uint32_t t0 = nzl, t1 = nzh;
-            nzl = fzl; nzh = fzh; fzl = t0; fzh = t1;
-        }
-        float tn[8];
-        uint32_t hm = 0;
-#define RR_SLOT(S)                                                                                        \
-    {                                                                                                     \
-        const float tnx = fmaf((float)slot_byte<S>(nxl, nxh), bx, ax);                                    \
-        const float tny = fmaf((float)slot_byte<S>(nyl, nyh), by, ay);                                    \
-        const float tnz = fmaf((float)slot_byte<S>(nzl, nzh), bz, az);                                    \
-        const float tfx = fmaf((float)slot_byte<S>(fxl, fxh), bx, ax);                                    \
-        const float tfy = fmaf((float)slot_byte<S>(fyl, fyh), by, ay);                                    \
-        const float tfz = fmaf((float)slot_byte<S>(fzl, fzh), bz, az);                                    \
-        const float t0 = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, tmin));                                         \
-        const float t1 = fminf(fminf(tfx, tfy), fminf(tfz, best));                                          \
-        tn[S] = t0;                                                                                       \
-        if (slot_byte<S>(meta_lo, meta_hi) != 0u && t0 <= t1) hm |= 1u << (S ^ negmask);                  \
-    }
-        RR_SLOT(0) RR_SLOT(1) RR_SLOT(2) RR_SLOT(3) RR_SLOT(4) RR_SLOT(5) RR_SLOT(6) RR_SLOT(7)
-#undef RR_SLOT
-        const int cnt = __popc(hm);
-        if (sp + cnt > (int)kTraceStack) {
-            atomicOr(a.err, RR_DEVERR_TRACE_STACK);
-            best_tri = kMiss;
-            best = __int_as_float(0x7f800000);
-            break;
-        }
-#define RR_PUSH(S)                                                                                        \
-    {                                                                                                     \
-        const uint32_t pos = S ^ negmask;                                                                 \
-        if ((hm >> pos) & 1u) {                                                                           \
-            const uint32_t meta = slot_byte<S>(meta_lo, meta_hi);                                         \
-            const uint32_t ref = meta >= 0xE0u                                                            \
-                                     ? child_base + (meta & 7u)                                           \
-                                     : (kLeafFlag | (((meta >> 5) - 1u) << 28) | (tri_base + (meta & 31u))); \
-            stack[sp + __popc(hm >> (pos + 1))] = make_uint2(ref, __float_as_uint(tn[S]));                \
-        }                                                                                                 \
-    }
-        RR_PUSH(0) RR_PUSH(1) RR_PUSH(2) RR_PUSH(3) RR_PUSH(4) RR_PUSH(5) RR_PUSH(6) RR_PUSH(7)
-#undef RR_PUSH
-        sp += cnt;
-    }
-    if (best_tri == kMiss) return make_float4(__int_as_float(0x7f800000), 0.0f, 0.0f, __uint_as_float(kMiss));
-    const float tr = refine_t(a, best_k, o, d);
-    return make_float4(isfinite(tr) ? tr : best, bu, bv, __uint_as_float(best_tri));
+// Byte k of a 32-bit word as the float 2^23 + byte: one byte permute puts the
+// byte in the mantissa of 2^23 (no integer-to-float conversion).
+template <int K>
+__device__ __forceinline__ float byte_plus_2p23(uint32_t w) {
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, (uint32_t)K | 0x7540u));
 }
+
+// Traversal state of the ray a lane is tracing.  Node groups (child base,
+// remaining hit mask in the near-to-far order of the ray's direction octant,
+// inner-child mask) are the stack entries: one push per level descended.
+struct RayState {
+    float4 o, d;
+    float idx, idy, idz;
+    uint32_t negmask;
+    float best, bu, bv;
+    uint32_t best_tri, best_k;
+    uint32_t g_base, g_hits, g_imask;
+    uint32_t t_base, t_hits, t_all;  // pending triangle group: base, bits to test, node's tribits
+    int sp;
+};
+
+__device__ __forceinline__ void ray_begin(RayState &r, const TraceArgs &a, float4 o, float4 d) {
+    r.o = o;
+    r.d = d;
+    r.idx = safe_inv(d.x);
+    r.idy = safe_inv(d.y);
+    r.idz = safe_inv(d.z);
+    r.negmask = (r.idx < 0.0f ? 1u : 0u) | (r.idy < 0.0f ? 2u : 0u) | (r.idz < 0.0f ? 4u : 0u);
+    r.best = d.w;
+    r.bu = 0.0f;
+    r.bv = 0.0f;
+    r.best_tri = kMiss;
+    r.best_k = 0u;
+    // the current node group starts as a virtual group holding only the root
+    r.g_base = 0u;
+    r.g_hits = (a.n_nodes > 0 && o.w <= d.w) ? 1u : 0u;
+    r.g_imask = 1u << r.negmask;
+    r.t_base = 0u;
+    r.t_hits = 0u;
+    r.t_all = 0u;
+    r.sp = 0;
+}
+
+// Stack entries are node groups: (child base, remaining hit mask in octant
+// order | inner-child mask << 8).
+
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// Node part of a traversal round: visit the nearest node of the current group
+// (its hit inner children become the current group, its hit leaves the
+// pending triangle group).
+__device__ __forceinline__ bool ray_visit_node(RayState &r, uint2 *stack, const TraceArgs &a) {
+    const float tmin = r.o.w;
+    const uint32_t pos = __ffs(r.g_hits) - 1u;
+    r.g_hits &= r.g_hits - 1u;
+    const uint32_t slot = pos ^ r.negmask;
+    const uint32_t node = r.g_base + __popc(r.g_imask & ((1u << slot) - 1u));
+    if (r.g_hits != 0u) {
+        if (r.sp >= (int)kTraceStack) return false;
+        stack[r.sp++] = make_uint2(r.g_base, r.g_hits | (r.g_imask << 8));
+    }
+    const float4 *np = a.nodes + 5 * (size_t)node;
+    const float4 f0 = __ldg(np), f1 = __ldg(np + 1), f2 = __ldg(np + 2), f3 = __ldg(np + 3), f4 = __ldg(np + 4);
+    const uint32_t ew = __float_as_uint(f0.w);
+    const float sx = __uint_as_float((ew & 0xFFu) << 23);
+    const float sy = __uint_as_float(((ew >> 8) & 0xFFu) << 23);
+    const float sz = __uint_as_float(((ew >> 16) & 0xFFu) << 23);
+    // plane of quantised value q: t = q*b + a.  The byte arrives as 2^23 + q, so
+    // the offset moves into a: a' = a - 2^23*b.  Rounding a' costs at most half
+    // a quantisation step, and every stored box is one step larger than the
+    // child it bounds.
+    const float bx = sx * r.idx, by = sy * r.idy, bz = sz * r.idz;
+    const float ax = fmaf(-8388608.0f, bx, (f0.x - r.o.x) * r.idx);
+    const float ay = fmaf(-8388608.0f, by, (f0.y - r.o.y) * r.idy);
+    const float az = fmaf(-8388608.0f, bz, (f0.z - r.o.z) * r.idz);
+    uint32_t nxl = __float_as_uint(f2.x), nxh = __float_as_uint(f2.y);
+    uint32_t nyl = __float_as_uint(f2.z), nyh = __float_as_uint(f2.w);
+    uint32_t nzl = __float_as_uint(f3.x), nzh = __float_as_uint(f3.y);
+    uint32_t fxl = __float_as_uint(f3.z), fxh = __float_as_uint(f3.w);
+    uint32_t fyl = __float_as_uint(f4.x), fyh = __float_as_uint(f4.y);
+    uint32_t fzl = __float_as_uint(f4.z), fzh = __float_as_uint(f4.w);
+    // for a negative direction the near plane is the box's high side
+    if (r.negmask & 1u) {
+        const uint32_t t0 = nxl, t1 = nxh;
+        nxl = fxl; nxh = fxh; fxl = t0; fxh = t1;
+    }
+    if (r.negmask & 2u) {
+        const uint32_t t0 = nyl, t1 = nyh;
+        nyl = fyl; nyh = fyh; fyl = t0; fyh = t1;
+    }
+    if (r.negmask & 4u) {
+        const uint32_t t0 = nzl, t1 = nzh;
+        nzl = fzl; nzh = fzh; fzl = t0; fzh = t1;
+    }
+    uint32_t hm = 0u;  // slot s: the ray meets the child's box within [tmin, best]
+    const float best = r.best;
+#define RR_SLOT(S)                                                                                      \
+    {                                                                                                   \
+        const uint32_t w_nx = (S) < 4 ? nxl : nxh, w_ny = (S) < 4 ? nyl : nyh, w_nz = (S) < 4 ? nzl : nzh; \
+        const uint32_t w_fx = (S) < 4 ? fxl : fxh, w_fy = (S) < 4 ? fyl : fyh, w_fz = (S) < 4 ? fzl : fzh; \
+        const float t0 = max3f(fmaf(byte_plus_2p23<(S) & 3>(w_nx), bx, ax),                              \
+                               fmaf(byte_plus_2p23<(S) & 3>(w_ny), by, ay),                              \
+                               fmaxf(fmaf(byte_plus_2p23<(S) & 3>(w_nz), bz, az), tmin));                \
+        const float t1 = min3f(fmaf(byte_plus_2p23<(S) & 3>(w_fx), bx, ax),                              \
+                               fmaf(byte_plus_2p23<(S) & 3>(w_fy), by, ay),                              \
+                               fminf(fmaf(byte_plus_2p23<(S) & 3>(w_fz), bz, az), best));                \
+        if (t0 <= t1) hm |= 1u << (S);                                                                  \
+    }
+    RR_SLOT(0) RR_SLOT(1) RR_SLOT(2) RR_SLOT(3) RR_SLOT(4) RR_SLOT(5) RR_SLOT(6) RR_SLOT(7)
+#undef RR_SLOT
+    const uint32_t imask = (ew >> 24) & 0xFFu, tribits = __float_as_uint(f1.z);
+    hm &= __float_as_uint(f1.w);  // used slots only
+    // inner children to octant positions: bit s -> bit s ^ negmask
+    uint32_t hits = hm & imask;
+    if (r.negmask & 1u) hits = ((hits & 0x55u) << 1) | ((hits >> 1) & 0x55u);
+    if (r.negmask & 2u) hits = ((hits & 0x33u) << 2) | ((hits >> 2) & 0x33u);
+    if (r.negmask & 4u) hits = ((hits & 0x0Fu) << 4) | (hits >> 4);
+    // leaves: slot bit s -> nibble s, keeping the triangles the nibble holds
+    uint32_t x = hm & ~imask;
+    x = (x | (x << 12)) & 0x000F000Fu;
+    x = (x | (x << 6)) & 0x03030303u;
+    x = (x | (x << 3)) & 0x11111111u;
+    const uint32_t tris = (x * 15u) & tribits;
+    r.g_base = __float_as_uint(f1.x);
+    r.g_hits = hits;
+    r.g_imask = imask;
+    r.t_base = __float_as_uint(f1.y);
+    r.t_hits = tris;
+    r.t_all = tribits;
+    return true;
+}
+
+// Tests every triangle of the pending group.
+__device__ __forceinline__ void ray_test_triangles(RayState &r, const TraceArgs &a) {
+    const float tmin = r.o.w;
+    while (r.t_hits != 0u) {
+        const uint32_t b = __ffs(r.t_hits) - 1u;
+        r.t_hits &= r.t_hits - 1u;
+        const uint32_t k = r.t_base + __popc(r.t_all & ((1u << b) - 1u));
+        const float4 *tp = a.tris + 3 * (size_t)k;
+        const float4 v0 = __ldg(tp), e1 = __ldg(tp + 1), e2 = __ldg(tp + 2);
+        const float4 d = r.d, o = r.o;
+        const float pvx = d.y * e2.z - d.z * e2.y;
+        const float pvy = d.z * e2.x - d.x * e2.z;
+        const float pvz = d.x * e2.y - d.y * e2.x;
+        const float det = e1.x * pvx + e1.y * pvy + e1.z * pvz;
+        if (det == 0.0f) continue;
+        const float inv = __frcp_rn(det);
+        const float tvx = o.x - v0.x, tvy = o.y - v0.y, tvz = o.z - v0.z;
+        const float u = (tvx * pvx + tvy * pvy + tvz * pvz) * inv;
+        if (!(u >= 0.0f && u <= 1.0f)) continue;
+        const float qvx = tvy * e1.z - tvz * e1.y;
+        const float qvy = tvz * e1.x - tvx * e1.z;
+        const float qvz = tvx * e1.y - tvy * e1.x;
+        const float v = (d.x * qvx + d.y * qvy + d.z * qvz) * inv;
+        if (!(v >= 0.0f && u + v <= 1.0f)) continue;
+        const float t = (e2.x * qvx + e2.y * qvy + e2.z * qvz) * inv;
+        if (t > tmin && t < r.best) {
+            r.best = t;
+            r.bu = u;
+            r.bv = v;
+            r.best_tri = __float_as_uint(v0.w);
+            r.best_k = k;
+        }
+    }
+}
+
+__device__ __forceinline__ float4 ray_result(const RayState &r, const TraceArgs &a) {
+    if (r.best_tri == kMiss) return make_float4(__int_as_float(0x7f800000), 0.0f, 0.0f, __uint_as_float(kMiss));
+    const float tr = refine_t(a, r.best_k, r.o, r.d);
+    return make_float4(isfinite(tr) ? tr : r.best, r.bu, r.bv, __uint_as_float(r.best_tri));
+}
+
+// Persistent warps: a warp takes kQueueBatch consecutive rays per queue fetch,
+// one per lane.
+constexpr uint32_t kQueueBatch = 32;
 
 __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceArgs a) {
     const uint32_t lane = threadIdx.x & 31u;
+    uint2 stack[kTraceStack];
     while (true) {
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(a.queue, kQueueBatch);
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
         if (base >= a.n) break;
 #pragma unroll 1
-        for (uint32_t r = 0; r < kQueueBatch; r += 32) {
-            const uint32_t i = base + r + lane;
-            if (i < a.n) a.hits[i] = trace_ray(a, __ldg(a.o_tmin + i), __ldg(a.d_tmax + i));
+        for (uint32_t k = 0; k < kQueueBatch; k += 32) {
+            const uint32_t i = base + k + lane;
+            if (i >= a.n) break;
+            RayState r;
+            ray_begin(r, a, __ldg(a.o_tmin + i), __ldg(a.d_tmax + i));
+            while (true) {
+                if (r.g_hits != 0u && !ray_visit_node(r, stack, a)) {
+                    atomicOr(a.err, RR_DEVERR_TRACE_STACK);
+                    r.best_tri = kMiss;
+                    break;
+                }
+                ray_test_triangles(r, a);
+                if (r.g_hits == 0u) {
+                    if (r.sp == 0) break;
+                    const uint2 e = stack[--r.sp];
+                    r.g_base = e.x;
+                    r.g_hits = e.y & 0xFFu;
+                    r.g_imask = (e.y >> 8) & 0xFFu;
+                }
+            }
+            a.hits[i] = ray_result(r, a);
         }
     }
     __syncthreads();

@@ -8,9 +8,9 @@
 
 namespace rr {
 
-// Traversal stack entries per thread.  The builder computes the worst case a
-// tree can need and rr_build_bvh refuses trees that exceed it.
-constexpr uint32_t kTraceStack = 96;
+// Traversal stack entries per thread: one node group per level descended.
+// rr_build_bvh refuses deeper trees.
+constexpr uint32_t kTraceStack = 32;
 
 struct HostBVH {
     std::vector<RRNode8> nodes;
