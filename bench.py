@@ -19,8 +19,10 @@ bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import time
@@ -40,6 +42,9 @@ BYTES_SORT = 8 + (KEY_BITS // RADIX_BITS) * 2 * (8 + 4) - 4   # 196 for 64-bit k
 BYTES_GATHER = 4 + 36 + 36
 BYTES_TRACE = 32 + 16
 BYTES_ACCUM = 32 + 16
+TRACE_PROFILE = os.path.join("profiles", "trace_kernel_config2_bounce3.md")
+TRACE_SOURCES = ["paper_2506_11273_gb300/csrc/rr_trace.cu", "paper_2506_11273_gb300/csrc/rr_trace.h",
+                 "paper_2506_11273_gb300/csrc/rr_common.cuh", "paper_2506_11273_gb300/csrc/rr_bvh.cpp"]
 
 
 def parse():
@@ -70,6 +75,24 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def measured_trace_traffic():
+    """DRAM bytes per trace launch from the committed ncu summary, or None when
+    the trace kernel's sources have changed since that capture."""
+    try:
+        text = open(os.path.join(ROOT, TRACE_PROFILE)).read()
+        h = hashlib.sha256()
+        for src in TRACE_SOURCES:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+    except OSError:
+        return None
+    m_bytes = re.search(r"traffic_bytes = (\d+)", text)
+    m_hash = re.search(r"traffic_source_sha256_16: ([0-9a-f]+)", text)
+    if not m_bytes or not m_hash or h.hexdigest()[:16] != m_hash.group(1):
+        return None
+    return int(m_bytes.group(1))
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples while the timed region runs."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -80,10 +103,11 @@ class ClockSampler:
         self.dev = device_index
         self.p = None
         self.out = None
+        self.path = "/tmp/rr_clocks_%d.csv" % os.getpid()
 
     def __enter__(self):
         try:
-            self.out = open(os.devnull if False else "/tmp/rr_clocks_%d.csv" % os.getpid(), "w")
+            self.out = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
                                        "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.out, stderr=subprocess.DEVNULL)
@@ -102,10 +126,9 @@ class ClockSampler:
             self.out.close()
 
     def summary(self):
-        path = "/tmp/rr_clocks_%d.csv" % os.getpid()
         try:
-            rows = [r.split(",") for r in open(path).read().strip().splitlines() if r.strip()]
-            os.remove(path)
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+            os.remove(self.path)
         except OSError:
             rows = []
         if not rows:
@@ -182,6 +205,8 @@ def run_ours(args):
                     keys=torch.empty(n, dtype=torch.int64, device=dev),
                     perm=torch.empty(n, dtype=torch.int32, device=dev),
                     ws=rr.sort_workspace(n, KEY_BITS, RADIX_BITS, dev),
+                    keys32=torch.empty(n, dtype=torch.int32, device=dev),
+                    ws32=rr.sort_workspace(n, 32, RADIX_BITS, dev),
                     so=torch.empty_like(o), sd=torch.empty_like(d), sp=torch.empty_like(p),
                     hits=torch.empty(n, 4, device=dev))
         return bufs
@@ -189,14 +214,15 @@ def run_ours(args):
     params_tp = rr.key_params(rr.RR_KEY_TWO_POINT, KEY_BITS, lo, hi, t_source=rr.RR_T_ADAPTIVE, table=table)
     params_aila = rr.key_params(rr.RR_KEY_AILA, KEY_BITS, lo, hi)
 
-    def make_step(B, params, accumulate):
+    def make_step(B, params, accumulate, bits=KEY_BITS):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        keys, ws = (B["keys"], B["ws"]) if bits > 32 else (B["keys32"], B["ws32"])
 
         def step():
             ev[0].record(stream)
-            rr.rr_compute_keys(B["o"], B["d"], params, B["keys"])
+            rr.rr_compute_keys(B["o"], B["d"], params, keys)
             ev[1].record(stream)
-            rr.rr_sort(B["keys"], None, B["perm"], B["n"], KEY_BITS, RADIX_BITS, B["ws"])
+            rr.rr_sort(keys, None, B["perm"], B["n"], bits, RADIX_BITS, ws)
             ev[2].record(stream)
             rr.rr_permute(B["o"], B["d"], B["p"], B["perm"], B["so"], B["sd"], B["sp"])
             ev[3].record(stream)
@@ -271,7 +297,14 @@ def run_ours(args):
     tot_a, _, ph_a = timed(step_aila, max(3, args.steps // 2), 3, phases_aila)
     aila = n * max(3, args.steps // 2) / (tot_a * 1e-3) / 1e6
     extra["aila_mrays"] = round(aila, 2)
-    extra["aila_trace_ms"] = float(np.median(np.array(ph_a)[:, 3]))
+    extra["aila_trace_ms"] = round(float(np.median(np.array(ph_a)[:, 3])), 4)
+    # the paper's 32-bit Two Point key (Table 1 uses 32-bit keys) on the same rays
+    params_tp32 = rr.key_params(rr.RR_KEY_TWO_POINT, 32, lo, hi, t_source=rr.RR_T_ADAPTIVE, table=table)
+    step_32, phases_32 = make_step(B, params_tp32, False, bits=32)
+    tot_32, _, ph_32 = timed(step_32, max(3, args.steps // 2), 3, phases_32)
+    extra["two_point_32bit_mrays"] = round(n * max(3, args.steps // 2) / (tot_32 * 1e-3) / 1e6, 2)
+    extra["two_point_32bit_phases_ms"] = {k: round(float(v), 4) for k, v in
+                                          zip(["key", "sort", "gather", "trace"], np.median(np.array(ph_32), axis=0)[:4])}
 
     if not args.no_extra:
         per_bounce = []
@@ -331,7 +364,8 @@ def run_ours(args):
         "speedup_vs_unsorted": round(value / unsorted, 3),
         "phases_ms": {k: round(v, 4) for k, v in phase_ms.items()},
         "roofline": {"bound": "hbm", "kernel": "trace", "achieved": round(trace_ach, 1), "peak": hbm,
-                     "unit": "GB/s", "frac": round(trace_ach / hbm, 4), "traffic": None,
+                     "unit": "GB/s", "frac": round(trace_ach / hbm, 4),
+                     "traffic": None if args.small else measured_trace_traffic(),
                      "peak_kind": peak_kind, "algorithmic_bytes_per_ray": BYTES_TRACE},
         "phase_roofline": {
             "key": {"gbs": round(key_ach, 1), "frac": round(key_ach / hbm, 3), "bytes_per_ray": BYTES_KEY},

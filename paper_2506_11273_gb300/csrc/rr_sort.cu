@@ -2,8 +2,8 @@
 // one upfront pass counts the digits of every pass; then each digit pass is a
 // single kernel in which a tile ranks its keys (peer masks from warp votes),
 // publishes its per-digit counts, resolves its global offsets by a
-// decoupled look-back over the preceding tiles (a window of predecessors read
-// at once), and scatters through shared memory so that global writes come out
+// decoupled look-back over the preceding tiles (pointer jumping over
+// published spans), and scatters through shared memory so that global writes come out
 // in runs.
 #include <algorithm>
 #include <mutex>
@@ -12,22 +12,25 @@
 
 namespace rr {
 
-constexpr uint32_t kFlagAgg = 1u << 30;     // word holds this tile's count only
-constexpr uint32_t kFlagPrefix = 2u << 30;  // word holds the count of tiles 0..this
-constexpr uint32_t kValMask = (1u << 30) - 1u;
+// Look-back word of (tile t, digit d): ready bit | first tile s of the span it
+// covers | count of digit d in tiles s..t.  A span starting at tile 0 is the
+// inclusive prefix.
+constexpr unsigned long long kReady = 1ull << 63;
 constexpr uint32_t kSpinLimit = 1u << 20;   // bounded wait on a predecessor's word
 constexpr int kSortBlock = 256;
 constexpr int kSortWarps = kSortBlock / 32;
 constexpr uint32_t kHistMaxBlocks = 512;    // blocks of the counting pass
-constexpr int kLookbackWindow = 16;         // predecessor tiles read per look-back round
 
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long lookback_word(uint32_t start, uint32_t count) {
+    return kReady | ((unsigned long long)start << 32) | count;
 }
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -90,6 +93,9 @@ __device__ __forceinline__ uint32_t scan_digits(uint32_t v, uint32_t *s_warp) {
 
 // ------------------------------------------------------------------ upfront histograms
 
+// Counts the digits of every pass over all keys.  Plain shared atomics into
+// two copies of the block's counters (even and odd warps): one atomic per key
+// and pass, far fewer instructions than building warp peer masks.
 template <typename K, int RBITS>
 __global__ void __launch_bounds__(kSortBlock) sort_histogram_kernel(const K *__restrict__ keys, uint32_t n,
                                                                    uint32_t bits, uint32_t passes,
@@ -99,40 +105,42 @@ __global__ void __launch_bounds__(kSortBlock) sort_histogram_kernel(const K *__r
                                                                    uint32_t *zero_err) {
     constexpr int RADIX = 1 << RBITS;
     constexpr int PMAX = (64 + RBITS - 1) / RBITS;
-    constexpr int KPT = 4;  // keys per lane per round
-    __shared__ uint32_t sh[PMAX * RADIX];
-    const uint32_t lane = threadIdx.x & 31u;
-    for (uint32_t i = threadIdx.x; i < PMAX * RADIX; i += kSortBlock) sh[i] = 0;
+    constexpr int KPT = 4;  // keys per thread per round
+    __shared__ uint32_t sh[2][PMAX * RADIX];
+    for (uint32_t i = threadIdx.x; i < 2 * PMAX * RADIX; i += kSortBlock) (&sh[0][0])[i] = 0;
     if (blockIdx.x == 0) {
         if (threadIdx.x < passes) counters[threadIdx.x] = 0u;  // tile counters of every pass
         if (threadIdx.x == 0 && zero_err) *zero_err = 0u;
     }
     __syncthreads();
+    uint32_t *mine = sh[(threadIdx.x >> 5) & 1u];
     const uint32_t stride = gridDim.x * kSortBlock * KPT;
-    for (uint32_t base = blockIdx.x * kSortBlock * KPT + (threadIdx.x & ~31u) * KPT; base < n; base += stride) {
+    for (uint32_t base = blockIdx.x * kSortBlock * KPT + threadIdx.x; base < n; base += stride) {
         K k[KPT];
-        uint32_t vmask[KPT];
 #pragma unroll
         for (int q = 0; q < KPT; ++q) {
-            const uint32_t i = base + q * 32 + lane;
+            const uint32_t i = base + q * kSortBlock;
             k[q] = i < n ? keys[i] : (K)0;
-            vmask[q] = __ballot_sync(0xFFFFFFFFu, i < n);
         }
-        for (uint32_t p = 0; p < passes; ++p) {
-            const uint32_t shift = p * RBITS;
-            const uint32_t mask = (1u << min((uint32_t)RBITS, bits - shift)) - 1u;
 #pragma unroll
-            for (int q = 0; q < KPT; ++q) {
-                const uint32_t dg = digit_of(k[q], shift, mask);
-                const uint32_t peers = digit_peers<RBITS>(dg, vmask[q]);
-                if (((vmask[q] >> lane) & 1u) && lane == (uint32_t)(__ffs(peers) - 1))
-                    atomicAdd(&sh[p * RADIX + dg], __popc(peers));
+        for (int q = 0; q < KPT; ++q) {
+            if (base + q * kSortBlock < n) {
+                K x = k[q];
+                uint32_t left = bits;
+                for (uint32_t p = 0; p < passes; ++p) {
+                    const uint32_t nb = min((uint32_t)RBITS, left);
+                    atomicAdd(&mine[p * RADIX + ((uint32_t)x & ((1u << nb) - 1u))], 1u);
+                    x >>= RBITS;
+                    left -= nb;
+                }
             }
         }
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < passes * RADIX; i += kSortBlock)
-        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+    for (uint32_t i = threadIdx.x; i < passes * RADIX; i += kSortBlock) {
+        const uint32_t c = sh[0][i] + sh[1][i];
+        if (c) atomicAdd(&hist[i], c);
+    }
     // the look-back words of every pass start at zero
     for (size_t i = (size_t)blockIdx.x * kSortBlock + threadIdx.x; i < zero_count; i += (size_t)gridDim.x * kSortBlock)
         zero_words[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -150,7 +158,7 @@ struct PassArgs {
     uint32_t shift;
     uint32_t mask;
     const uint32_t *hist;     // RADIX counts of this pass's digit over all keys
-    uint32_t *lookback;       // [tiles][RADIX]
+    unsigned long long *lookback;  // [tiles][RADIX] look-back words
     uint32_t *tile_counter;
     uint32_t *err;
 };
@@ -219,52 +227,34 @@ __global__ void __launch_bounds__(kSortBlock, 3) onesweep_kernel(PassArgs<K> a) 
             s_wh[w * RADIX + tid] = cnt;
             cnt += c;
         }
-        st_relaxed(a.lookback + (size_t)tile * RADIX + tid, (tile == 0 ? kFlagPrefix : kFlagAgg) | cnt);
+        st_relaxed(a.lookback + (size_t)tile * RADIX + tid, lookback_word(tile, cnt));
     }
     const uint32_t dstart = scan_digits<RADIX>(tid < RADIX ? a.hist[tid] : 0u, s_misc + 8);
     const uint32_t lstart = scan_digits<RADIX>(cnt, s_misc + 8);
     uint32_t excl = 0;
     if (tid < RADIX) {
         if (tile > 0) {
-            // decoupled look-back over a window of predecessors at a time: sum
-            // their counts from the nearest one back until a word holds a
-            // prefix; restart from a predecessor that has not published yet
-            int j = (int)tile - 1;
-            uint32_t spins = 0;
-            while (true) {
-                uint32_t w[kLookbackWindow];
-#pragma unroll
-                for (int q = 0; q < kLookbackWindow; ++q)
-                    w[q] = (j - q >= 0) ? ld_relaxed(a.lookback + (size_t)(j - q) * RADIX + tid) : kFlagPrefix;
-                int status = 0, stop = 0;  // 0: keep going back, 1: prefix found, 2: not yet published
-                uint32_t add = 0;
-#pragma unroll
-                for (int q = 0; q < kLookbackWindow; ++q) {
-                    if (status == 0) {
-                        const uint32_t fl = w[q] & ~kValMask;
-                        if (fl == 0u) {
-                            status = 2;
-                            stop = q;
-                        } else {
-                            add += w[q] & kValMask;
-                            if (fl == kFlagPrefix) status = 1;
-                        }
+            // decoupled look-back by pointer jumping: add the span the nearest
+            // uncovered predecessor has published and continue before its
+            // start; republish the wider span so successors can jump over it.
+            // Spans grow as tiles finish, so a tile needs few hops even when
+            // every tile of the pass runs at the same time.
+            uint32_t start = tile, sum = cnt, spins = 0;
+            while (start > 0) {
+                const unsigned long long w = ld_relaxed(a.lookback + (size_t)(start - 1) * RADIX + tid);
+                if (!(w & kReady)) {
+                    if (++spins > kSpinLimit) {
+                        atomicOr(a.err, RR_DEVERR_LOOKBACK_TIMEOUT);
+                        break;
                     }
-                }
-                excl += add;
-                if (status == 1) break;
-                if (status == 0) {
-                    j -= kLookbackWindow;
+                    __nanosleep(32);
                     continue;
                 }
-                j -= stop;
-                if (++spins > kSpinLimit) {
-                    atomicOr(a.err, RR_DEVERR_LOOKBACK_TIMEOUT);
-                    break;
-                }
-                __nanosleep(32);
+                sum += (uint32_t)w;
+                start = (uint32_t)(w >> 32) & 0x7FFFFFFFu;
+                st_relaxed(a.lookback + (size_t)tile * RADIX + tid, lookback_word(start, sum));
             }
-            st_relaxed(a.lookback + (size_t)tile * RADIX + tid, kFlagPrefix | ((excl + cnt) & kValMask));
+            excl = sum - cnt;
         }
         s_lstart[tid] = lstart;
         s_gbase[tid] = dstart + excl - lstart;
@@ -301,7 +291,7 @@ struct SortPlan {
 };
 
 // Workspace layout: digit counts [pass][radix], tile counters [pass],
-// look-back words [pass][tile][radix], two key buffers and one value buffer.
+// 64-bit look-back words [pass][tile][radix], two key buffers, one value buffer.
 constexpr SortPlan plan_sort(uint32_t n, uint32_t bits, uint32_t radix_bits) {
     SortPlan p{};
     p.passes = (bits + radix_bits - 1) / radix_bits;
@@ -315,7 +305,7 @@ constexpr SortPlan plan_sort(uint32_t n, uint32_t bits, uint32_t radix_bits) {
     p.off_counters = off;
     off = align256(off + sizeof(uint32_t) * p.passes);
     p.off_lookback = off;
-    off = align256(off + sizeof(uint32_t) * (size_t)p.passes * p.tiles * p.radix);
+    off = align256(off + sizeof(unsigned long long) * (size_t)p.passes * p.tiles * p.radix);
     p.off_keys_a = off;
     off = align256(off + (size_t)p.kb * n);
     p.off_keys_b = off;
@@ -342,14 +332,14 @@ static cudaError_t enqueue_sort(const SortPlan &pl, const K *keys_in, K *keys_ou
                                 int sm_count, cudaStream_t s) {
     uint32_t *hist = reinterpret_cast<uint32_t *>(ws + pl.off_hist);
     uint32_t *counters = reinterpret_cast<uint32_t *>(ws + pl.off_counters);
-    uint32_t *lookback = reinterpret_cast<uint32_t *>(ws + pl.off_lookback);
+    unsigned long long *lookback = reinterpret_cast<unsigned long long *>(ws + pl.off_lookback);
     K *keys_a = reinterpret_cast<K *>(ws + pl.off_keys_a);
     K *keys_b = reinterpret_cast<K *>(ws + pl.off_keys_b);
     uint32_t *vals_ws = reinterpret_cast<uint32_t *>(ws + pl.off_vals);
 
     cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * pl.passes * pl.radix, s);
     if (e != cudaSuccess) return e;
-    const size_t zero_count = (size_t)pl.passes * pl.tiles * pl.radix / 4;
+    const size_t zero_count = (size_t)pl.passes * pl.tiles * pl.radix / 2;  // uint4 = two words
     const uint32_t per_block = kSortBlock * 4u;
     const uint32_t hist_blocks = std::max(
         1u, std::min({(n + per_block - 1) / per_block, 2u * (uint32_t)sm_count, kHistMaxBlocks}));
