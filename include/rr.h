@@ -216,6 +216,17 @@ rr_status rr_bvh_get_info(const rr_bvh *bvh, rr_bvh_info *info);
 rr_status rr_trace(const rr_bvh *bvh, const float *o_tmin, const float *d_tmax, uint32_t n,
                    float *hits_out, void *stream);
 
+/*
+ * rr_trace_accumulate - rr_trace and, in the same kernel, the length-table
+ * update of rr_length_table_accumulate for the traced rays (Section 3.1.6: the
+ * table is updated after each trace pass).  Same hits and same table contents
+ * as rr_trace followed by rr_length_table_accumulate on the same rays; the rays
+ * and hits are not read a second time.  table: a table created for the box the
+ * caller quantises with (the usual rr_length_table rules apply).
+ */
+rr_status rr_trace_accumulate(const rr_bvh *bvh, const float *o_tmin, const float *d_tmax,
+                              uint32_t n, float *hits_out, rr_length_table *table, void *stream);
+
 /* ---------------------------------------------------------------- ray-length table */
 
 /*

@@ -99,6 +99,38 @@ __device__ __forceinline__ void quantise_ray(const QuantFrame &f, float4 o, floa
     for (int c = 0; c < 3; ++c) qd[c] = quantise_unit(__fmul_rn(__fadd_rn(dh[c], 1.0f), 0.5f));
 }
 
+// The frame of a box, computed once per block into shared memory by thread 0.
+// Call from every thread of the block.
+__device__ __forceinline__ QuantFrame block_frame(const float lo[3], const float hi[3]) {
+    __shared__ QuantFrame s_frame;
+    if (threadIdx.x == 0) s_frame = make_frame(lo, hi);
+    __syncthreads();
+    return s_frame;
+}
+
+// floor(sum / cnt) for cnt >= 1 and a quotient below 2^32: a float estimate,
+// one refinement from the remainder, then exact integer correction of the
+// remaining +-1 (instead of a 64-bit integer division).
+__device__ __forceinline__ uint32_t div_floor_u64(unsigned long long sum, unsigned long long cnt) {
+    const float inv = __frcp_rn(__ull2float_rn(cnt));
+    long long q = (long long)(__ull2float_rn(sum) * inv);
+    if (q < 0) q = 0;
+    long long r = (long long)(sum - (unsigned long long)q * cnt);
+    q += (long long)(__ll2float_rn(r) * inv);
+    r = (long long)(sum - (unsigned long long)q * cnt);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (r < 0) {
+            --q;
+            r += (long long)cnt;
+        } else if (r >= (long long)cnt) {
+            ++q;
+            r -= (long long)cnt;
+        }
+    }
+    return (uint32_t)q;
+}
+
 // 20-bit compacted Aila code: the length-table cell (Section 3.1.6).
 __device__ __forceinline__ uint32_t table_cell(const uint32_t qo[3], const uint32_t qd[3]) {
     uint32_t c[6] = {qo[0], qo[1], qo[2], qd[0] >> 3, qd[1] >> 3, qd[2] >> 3};

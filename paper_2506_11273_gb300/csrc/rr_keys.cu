@@ -23,9 +23,9 @@ struct KeyArgs {
 // One ray per thread: two 16-byte loads, quantisation, interleave, one store.
 template <int LAYOUT, int TSRC, typename KeyT>
 __global__ void __launch_bounds__(256) key_kernel(KeyArgs a) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const QuantFrame f = block_frame(a.lo, a.hi);
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    const QuantFrame f = make_frame(a.lo, a.hi);
     float4 o = __ldg(a.o_tmin + i);
     float4 d = __ldg(a.d_tmax + i);
     uint32_t qo[3], qd[3];
@@ -44,8 +44,8 @@ __global__ void __launch_bounds__(256) key_kernel(KeyArgs a) {
             if (cell.y == 0ull) {
                 t = __fmul_rn(0.25f, f.E);
             } else {
-                unsigned long long mean = cell.x / cell.y;
-                t = __fmul_rn(__fmul_rn(__ull2float_rn(mean), 5.9604644775390625e-8f), f.E);
+                const uint32_t mean = div_floor_u64(cell.x, cell.y);
+                t = __fmul_rn(__fmul_rn(__uint2float_rn(mean), 5.9604644775390625e-8f), f.E);
             }
         }
         if (!isfinite(t)) t = __fmul_rn(4.0f, f.E);
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256) table_accumulate_kernel(unsigned long lon
                                                                const float4 *d_tmax, const float4 *hits,
                                                                uint32_t n) {
     const float lo[3] = {lo0, lo1, lo2}, hi[3] = {hi0, hi1, hi2};
-    const QuantFrame f = make_frame(lo, hi);
+    const QuantFrame f = block_frame(lo, hi);
     const float invE = __fdiv_rn(1.0f, f.E);
     const uint32_t lane = threadIdx.x & 31u;
     uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;  // warp-uniform

@@ -105,12 +105,10 @@ extern "C" rr_status rr_pipeline_run(rr_pipeline *p, const float *o_tmin, const 
     if (st != RR_OK) return st;
     st = rr_permute(o_tmin, d_tmax, payload_in, p->perm, n, p->o_sorted, p->d_sorted, payload_out, stream);
     if (st != RR_OK) return st;
-    st = rr_trace(p->bvh, p->o_sorted, p->d_sorted, n, hits_out, stream);
-    if (st != RR_OK) return st;
     if (p->params.layout == RR_KEY_TWO_POINT && p->params.t_source == RR_T_ADAPTIVE)
-        st = rr_length_table_accumulate(const_cast<rr_length_table *>(p->params.table), p->o_sorted, p->d_sorted,
-                                        hits_out, n, stream);
-    return st;
+        return rr_trace_accumulate(p->bvh, p->o_sorted, p->d_sorted, n, hits_out,
+                                   const_cast<rr_length_table *>(p->params.table), stream);
+    return rr_trace(p->bvh, p->o_sorted, p->d_sorted, n, hits_out, stream);
 }
 
 extern "C" rr_status rr_pipeline_run_host(rr_pipeline *p, const float *o_host, const float *d_host,

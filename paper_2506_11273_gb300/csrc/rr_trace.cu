@@ -13,6 +13,7 @@
 #include <cmath>
 
 #include "rr_common.cuh"
+#include "rr_keymath.cuh"
 #include "rr_trace.h"
 
 namespace rr {
@@ -30,6 +31,8 @@ struct TraceArgs {
     uint32_t n_nodes;
     uint32_t *queue;  // [0] next ray, [1] finished blocks
     uint32_t *err;
+    unsigned long long *table;  // length-table cells {sum, count} (accumulating kernel only)
+    float tlo[3], thi[3];       // the table's box
 };
 
 __device__ __forceinline__ float safe_inv(float x) {
@@ -261,9 +264,33 @@ __device__ __forceinline__ float4 ray_result(const RayState &r, const TraceArgs 
 // one per lane.
 constexpr uint32_t kQueueBatch = 32;
 
+// The length-table update of one traced ray (Section 3.1.6), the arithmetic of
+// table_accumulate_kernel: a ray that hit adds trunc(clamp(t*|d|/E, 0, 64)*2^24)
+// and one count to the cell of its 20-bit compacted Aila code.
+__device__ __forceinline__ void accumulate_hit(const TraceArgs &a, const QuantFrame &f, float invE, float4 o,
+                                               float4 d, float4 h) {
+    if (__float_as_uint(h.w) == kMiss || !isfinite(h.x)) return;
+    uint32_t qo[3], qd[3];
+    float dh[3];
+    quantise_ray(f, o, d, qo, qd, dh);
+    const uint32_t cell = table_cell(qo, qd);
+    float x = __fmul_rn(__fmul_rn(h.x, length3(d.x, d.y, d.z)), invE);
+    if (!(x > 0.0f)) x = 0.0f;
+    if (x > 64.0f) x = 64.0f;
+    atomicAdd(a.table + 2 * (size_t)cell, (unsigned long long)__float2uint_rz(__fmul_rn(x, 16777216.0f)));
+    atomicAdd(a.table + 2 * (size_t)cell + 1, 1ull);
+}
+
+template <bool ACCUM>
 __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceArgs a) {
     const uint32_t lane = threadIdx.x & 31u;
     uint2 stack[kTraceStack];
+    QuantFrame f;
+    float invE = 0.0f;
+    if (ACCUM) {
+        f = make_frame(a.tlo, a.thi);
+        invE = __fdiv_rn(1.0f, f.E);
+    }
     while (true) {
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(a.queue, kQueueBatch);
@@ -274,7 +301,8 @@ __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceArgs a) {
             const uint32_t i = base + k + lane;
             if (i >= a.n) break;
             RayState r;
-            ray_begin(r, a, __ldg(a.o_tmin + i), __ldg(a.d_tmax + i));
+            const float4 o = __ldg(a.o_tmin + i), d = __ldg(a.d_tmax + i);
+            ray_begin(r, a, o, d);
             while (true) {
                 if (r.g_hits != 0u && !ray_visit_node(r, stack, a)) {
                     atomicOr(a.err, RR_DEVERR_TRACE_STACK);
@@ -290,7 +318,9 @@ __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceArgs a) {
                     r.g_imask = (e.y >> 8) & 0xFFu;
                 }
             }
-            a.hits[i] = ray_result(r, a);
+            const float4 h = ray_result(r, a);
+            a.hits[i] = h;
+            if (ACCUM) accumulate_hit(a, f, invE, o, d, h);
         }
     }
     __syncthreads();
@@ -382,22 +412,27 @@ extern "C" rr_status rr_bvh_get_info(const rr_bvh *b, rr_bvh_info *info) {
     return RR_OK;
 }
 
-extern "C" rr_status rr_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax, uint32_t n, float *hits_out,
-                              void *stream) {
-    if (!b) return fail(RR_ERR_INVALID_ARG, "rr_trace: NULL bvh");
+namespace {
+
+rr_status launch_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax, uint32_t n, float *hits_out,
+                       rr_length_table *table, void *stream, const char *what) {
+    if (!b) return fail(RR_ERR_INVALID_ARG, std::string(what) + ": NULL bvh");
     if (n == 0) return RR_OK;
-    if (!o_tmin || !d_tmax || !hits_out) return fail(RR_ERR_INVALID_ARG, "rr_trace: NULL buffer");
+    if (!o_tmin || !d_tmax || !hits_out) return fail(RR_ERR_INVALID_ARG, std::string(what) + ": NULL buffer");
     if (!aligned16(o_tmin) || !aligned16(d_tmax) || !aligned16(hits_out))
-        return fail(RR_ERR_INVALID_ARG, "rr_trace: buffers not 16-byte aligned");
+        return fail(RR_ERR_INVALID_ARG, std::string(what) + ": buffers not 16-byte aligned");
     if (overlaps(hits_out, 16ull * n, o_tmin, 16ull * n) || overlaps(hits_out, 16ull * n, d_tmax, 16ull * n))
-        return fail(RR_ERR_INVALID_ARG, "rr_trace: hits overlap the rays");
+        return fail(RR_ERR_INVALID_ARG, std::string(what) + ": hits overlap the rays");
     rr_status st;
     DeviceState *ds = device_state(&st);
     if (!ds) return st;
-    static int blocks_per_sm = 0;
-    if (blocks_per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, trace_kernel, kTraceBlock, 0);
-        if (e != cudaSuccess || blocks_per_sm < 1) blocks_per_sm = 1;
+    static int blocks_per_sm[2] = {0, 0};
+    const int acc = table ? 1 : 0;
+    if (blocks_per_sm[acc] == 0) {
+        int bps = 0;
+        cudaError_t e = acc ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, trace_kernel<true>, kTraceBlock, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, trace_kernel<false>, kTraceBlock, 0);
+        blocks_per_sm[acc] = (e != cudaSuccess || bps < 1) ? 1 : bps;
     }
     const uint32_t slot = ds->next_counter.fetch_add(1) % (kCounterPool / 2);
     TraceArgs a;
@@ -411,10 +446,31 @@ extern "C" rr_status rr_trace(const rr_bvh *b, const float *o_tmin, const float 
     a.n_nodes = b->n_nodes;
     a.queue = ds->counters + 2 * slot;
     a.err = ds->err;
+    a.table = table ? table->cells : nullptr;
+    for (int c = 0; c < 3; ++c) {
+        a.tlo[c] = table ? table->box.lo[c] : 0.0f;
+        a.thi[c] = table ? table->box.hi[c] : 0.0f;
+    }
     const uint32_t want = (n + kQueueBatch - 1) / kQueueBatch;  // warps that can get work
-    uint32_t grid = (uint32_t)ds->sm_count * (uint32_t)blocks_per_sm;
+    uint32_t grid = (uint32_t)ds->sm_count * (uint32_t)blocks_per_sm[acc];
     grid = std::max(1u, std::min(grid, (want + kTraceBlock / 32 - 1) / (kTraceBlock / 32)));
-    trace_kernel<<<grid, kTraceBlock, 0, as_stream(stream)>>>(a);
+    if (table)
+        trace_kernel<true><<<grid, kTraceBlock, 0, as_stream(stream)>>>(a);
+    else
+        trace_kernel<false><<<grid, kTraceBlock, 0, as_stream(stream)>>>(a);
     note_launches(1);
-    return check_launch("rr_trace");
+    return check_launch(what);
+}
+
+}  // namespace
+
+extern "C" rr_status rr_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax, uint32_t n, float *hits_out,
+                              void *stream) {
+    return launch_trace(b, o_tmin, d_tmax, n, hits_out, nullptr, stream, "rr_trace");
+}
+
+extern "C" rr_status rr_trace_accumulate(const rr_bvh *b, const float *o_tmin, const float *d_tmax, uint32_t n,
+                                         float *hits_out, rr_length_table *table, void *stream) {
+    if (!table) return fail(RR_ERR_INVALID_ARG, "rr_trace_accumulate: NULL table");
+    return launch_trace(b, o_tmin, d_tmax, n, hits_out, table, stream, "rr_trace_accumulate");
 }

@@ -39,7 +39,7 @@ RR_SORT_NOALLOC_MAX_N = 1 << 20
 # every symbol include/rr.h declares
 EXPORTS = [
     "rr_compute_keys", "rr_sort_workspace_size", "rr_sort", "rr_permute", "rr_build_bvh",
-    "rr_bvh_destroy", "rr_bvh_get_info", "rr_trace", "rr_length_table_create",
+    "rr_bvh_destroy", "rr_bvh_get_info", "rr_trace", "rr_trace_accumulate", "rr_length_table_create",
     "rr_length_table_reset", "rr_length_table_accumulate", "rr_length_table_read",
     "rr_length_table_write", "rr_length_table_destroy", "rr_pipeline_create",
     "rr_pipeline_destroy", "rr_pipeline_run", "rr_pipeline_run_host", "rr_device_error",
@@ -84,6 +84,7 @@ def lib():
             L.rr_bvh_destroy.argtypes = [vp]
             L.rr_bvh_get_info.argtypes = [vp, C.POINTER(BvhInfo)]
             L.rr_trace.argtypes = [vp, vp, vp, u32, vp, vp]
+            L.rr_trace_accumulate.argtypes = [vp, vp, vp, u32, vp, vp, vp]
             L.rr_length_table_create.argtypes = [C.POINTER(C.c_float), C.POINTER(C.c_float),
                                                  C.POINTER(vp), vp]
             L.rr_length_table_reset.argtypes = [vp, vp]
@@ -246,6 +247,13 @@ def rr_trace(bvh: BVH, o_tmin, d_tmax, hits_out, n: int | None = None, stream=No
     n = o_tmin.shape[0] if n is None else n
     _check(lib().rr_trace(bvh.handle, _ptr(o_tmin), _ptr(d_tmax), n, _ptr(hits_out),
                           _stream(stream)), "rr_trace")
+
+
+def rr_trace_accumulate(bvh: BVH, o_tmin, d_tmax, hits_out, table: "LengthTable", n: int | None = None,
+                        stream=None):
+    n = o_tmin.shape[0] if n is None else n
+    _check(lib().rr_trace_accumulate(bvh.handle, _ptr(o_tmin), _ptr(d_tmax), n, _ptr(hits_out),
+                                     table.handle, _stream(stream)), "rr_trace_accumulate")
 
 
 # ---------------------------------------------------------------- ray-length table

@@ -304,3 +304,25 @@ def test_full_size_keys_and_sort_config2():
             perm, _ = gpu_sort(k_or, bits, 8, want_keys=False)
             assert np.array_equal(perm, perm_or)
     assert_no_device_error()
+
+
+def test_adaptive_keys_with_extreme_table_contents(soup):
+    """Cells with large sums and counts (the estimate divides a 64-bit sum by
+    a count): keys still match the oracle reading the same table."""
+    tris, rays, lo, hi = soup
+    E = oracle.largest_extent(lo, hi)
+    rng = np.random.default_rng(17)
+    cnt = rng.integers(1, 2 ** 32 - 1, size=1 << 20, dtype=np.uint64).astype(np.uint32)
+    cnt[::3] = rng.integers(1, 50, size=cnt[::3].size).astype(np.uint32)
+    mean = rng.integers(0, 2 ** 30, size=1 << 20, dtype=np.uint64)
+    extra = (rng.random(1 << 20) * cnt).astype(np.uint64)
+    s = mean * cnt.astype(np.uint64) + extra
+    tab = rr.LengthTable(lo, hi)
+    tab.write(s, cnt)
+    ot = oracle.LengthTable(E)
+    ot.sum[:] = s
+    ot.cnt[:] = cnt
+    k_gpu = gpu_keys(rays, rr.RR_KEY_TWO_POINT, 64, lo, hi, tsrc=rr.RR_T_ADAPTIVE, table=tab)
+    k_or = oracle.compute_keys(oracle.TWO_POINT, 64, rays.o_tmin, rays.d_tmax, lo, hi, tsrc=oracle.T_ADAPTIVE,
+                               table=ot)
+    assert np.array_equal(k_gpu, k_or)

@@ -240,3 +240,24 @@ def test_pipeline_rejects_bad_arguments():
         pipe.run(o, d, p, hits, torch.empty_like(p))  # n > max_n
     with pytest.raises(rr.RRError):
         rr.Pipeline(bvh, 100, params, radix_bits=6)
+
+
+def test_trace_accumulate_equals_trace_then_accumulate():
+    """The fused kernel gives the same hits and the same table as the two calls."""
+    tris = W.scene_box_soup(seed=1)
+    rays = W.rays_box_soup(tris, n=65536, seed=4)
+    lo, hi = W.scene_aabb(tris)
+    bvh = rr.BVH(tris)
+    o, d, _ = rr.to_device_rays(rays)
+    t1, t2 = rr.LengthTable(lo, hi), rr.LengthTable(lo, hi)
+    h1 = torch.empty(len(rays), 4, device="cuda")
+    h2 = torch.empty(len(rays), 4, device="cuda")
+    rr.rr_trace(bvh, o, d, h1)
+    rr.rr_length_table_accumulate(t1, o, d, h1)
+    rr.rr_trace_accumulate(bvh, o, d, h2, t2)
+    torch.cuda.synchronize()
+    assert np.array_equal(h1.cpu().numpy().view(np.uint32), h2.cpu().numpy().view(np.uint32))
+    s1, c1 = t1.read()
+    s2, c2 = t2.read()
+    assert np.array_equal(s1, s2) and np.array_equal(c1, c2)
+    assert int(c2.sum()) > (1 << 20)
