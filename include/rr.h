@@ -63,8 +63,14 @@ typedef enum {
     RR_KEY_AILA = 0,         /* origin and direction interleaved; each quantised direction
                                 component has three leading zero bits (Section 3.1.4) */
     RR_KEY_AILA_COMPACT = 1, /* the same bits with the leading zeros removed (Section 3.1.4) */
-    RR_KEY_TWO_POINT = 2     /* origin and estimated termination point interleaved,
+    RR_KEY_TWO_POINT = 2,    /* origin and estimated termination point interleaved,
                                 origin first in every level (Section 3.1.5) */
+    RR_KEY_ORIGIN = 3,       /* 3D Morton code of the origin only (Section 3.1.1) */
+    RR_KEY_REIS = 4,         /* origin bits, then direction bits: 22 + 10 at 32 bits, the same
+                                ratio at other lengths (Section 3.1.2) */
+    RR_KEY_COSTA = 5,        /* direction bits, then origin bits: 8 + 24 at 32 bits (Section 3.1.3) */
+    RR_KEY_OCTAHEDRON = 6    /* origin interleaved with the octahedral 2D direction (Meyer et
+                                al. 2010), compacted as Aila (Section 3.1.4, Figure 2) */
 } rr_key_layout;
 
 /* Termination estimate of the Two Point key (Section 3.1.6). */
@@ -110,7 +116,11 @@ typedef struct {
  * clamped, and quantised to 32 bits by truncation.  Directions are normalised
  * and mapped from [-1,1] to [0,1].  The Aila layouts interleave origin and
  * direction (the direction shifted right by 3: its three leading zero bits);
- * the compact layout drops the nine zero bits.  The Two Point layout
+ * the compact layout drops the nine zero bits.  The origin, Reis and Costa
+ * layouts take prefixes of the 3D Morton strings of the origin and of the
+ * direction; the octahedron layout interleaves the origin with the two
+ * octahedral coordinates of the direction (each shifted right by 4, the
+ * zero slots dropped).  The Two Point layout
  * interleaves the origin with p = o + t_est * normalize(d), where t_est comes
  * from params->t_source; a non-finite t_est is replaced by 4 * E.  The key is
  * the first `bits` bits of the 192-bit interleaved string, x before y before z.
@@ -280,6 +290,23 @@ rr_status rr_pipeline_run(rr_pipeline *p, const float *o_tmin, const float *d_tm
 rr_status rr_pipeline_run_host(rr_pipeline *p, const float *o_tmin_host, const float *d_tmax_host,
                                const uint32_t *payload_host, uint32_t n, float *hits_host,
                                uint32_t *payload_out_host, void *stream);
+
+/* ---------------------------------------------------------------- coherence measure */
+
+/*
+ * rr_coherence_capsule - the capsule coherence measure of Section 4.3.  For
+ * each run of `subset` consecutive rays (1..64; the paper uses 64) the capsule
+ * is fitted as follows: its axis joins the centroid of the origins and the
+ * centroid of the termination points o + normalize(d) * t (t from hits; a miss
+ * ends at 4 * E); its radii are the mean distances of the origins and of the
+ * termination points from that axis; its area is two hemispheres plus the
+ * lateral area of the cone frustum between them.  areas_out (device) receives
+ * one float per run: n / subset runs (a shorter tail is ignored), or one run
+ * when n < subset.  The mean of the areas is the paper's coherence value; lower
+ * means more coherent.  fp32 arithmetic.
+ */
+rr_status rr_coherence_capsule(const float *o_tmin, const float *d_tmax, const float *hits, uint32_t n,
+                               uint32_t subset, float E, float *areas_out, void *stream);
 
 /* ---------------------------------------------------------------- diagnostics */
 

@@ -21,7 +21,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-AILA, AILA_COMPACT, TWO_POINT = 0, 1, 2
+AILA, AILA_COMPACT, TWO_POINT, ORIGIN, REIS, COSTA, OCTAHEDRON = 0, 1, 2, 3, 4, 5, 6
 T_FIXED, T_ADAPTIVE, T_GIVEN = 0, 1, 2
 MISS = 0xFFFFFFFF
 TABLE_CELLS = 1 << 20
@@ -72,6 +72,15 @@ def lib():
             L.or_compute_keys.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_float, _f32p, _f32p,
                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_float, _f32p,
                                           _f32p, C.c_uint32, _u64p]
+            L.or_morton3_prefix.restype = C.c_uint64
+            L.or_morton3_prefix.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]
+            L.or_octahedral.argtypes = [_f32p, C.POINTER(C.c_float), C.POINTER(C.c_float)]
+            L.or_interleave_od.restype = C.c_uint64
+            L.or_interleave_od.argtypes = [C.c_int, _u32p, C.c_uint32]
+            L.or_key_od.restype = C.c_uint64
+            L.or_key_od.argtypes = [C.c_int, C.c_uint32, _f32p, _f32p, _f32p, _f32p]
+            L.or_capsule_areas.restype = C.c_uint32
+            L.or_capsule_areas.argtypes = [_f32p, _f32p, _f32p, C.c_uint32, C.c_uint32, C.c_float, _f64p]
             L.or_stable_sort.restype = C.c_int
             L.or_stable_sort.argtypes = [_u64p, C.c_uint32, _u32p, _u64p]
             L.or_permute.argtypes = [_f32p, _f32p, _u32p, _u32p, C.c_uint32, _f32p, _f32p, _u32p]
@@ -129,6 +138,26 @@ def interleave(layout: int, comp, bits: int) -> int:
 def key(layout: int, bits: int, o, d, t_est, lo, hi) -> int:
     return int(lib().or_key(layout, bits, _f32(o, 3), _f32(d, 3), float(np.float32(t_est)),
                             _f32(lo, 3), _f32(hi, 3)))
+
+
+def morton3_prefix(c0, c1, c2, bits) -> int:
+    return int(lib().or_morton3_prefix(int(c0), int(c1), int(c2), bits))
+
+
+def octahedral(d):
+    u, v = C.c_float(), C.c_float()
+    lib().or_octahedral(_f32(d, 3), C.byref(u), C.byref(v))
+    return np.float32(u.value), np.float32(v.value)
+
+
+def interleave_od(layout: int, comp, bits: int) -> int:
+    c = np.zeros(6, np.uint32)
+    c[:len(comp)] = comp
+    return int(lib().or_interleave_od(layout, c, bits))
+
+
+def key_od(layout: int, bits: int, o, d, lo, hi) -> int:
+    return int(lib().or_key_od(layout, bits, _f32(o, 3), _f32(d, 3), _f32(lo, 3), _f32(hi, 3)))
 
 
 # ---------------------------------------------------------------- length table
@@ -259,6 +288,16 @@ class BVH:
         if getattr(self, "h", None):
             lib().or_bvh_free(self.h)
             self.h = None
+
+
+def capsule_areas(o_tmin, d_tmax, hits, E, subset: int = 64) -> np.ndarray:
+    """Capsule surface area of each consecutive subset of rays (Section 4.3)."""
+    o_tmin = _f32(o_tmin).reshape(-1, 4)
+    n = o_tmin.shape[0]
+    out = np.zeros(max(1, n // max(subset, 1) + 1), np.float64)
+    k = lib().or_capsule_areas(o_tmin, _f32(d_tmax).reshape(-1, 4), _f32(hits).reshape(-1, 4), n, subset,
+                               float(np.float32(E)), out)
+    return out[:k]
 
 
 def hit_tri(hits) -> np.ndarray:

@@ -15,6 +15,8 @@
  *   - compacted Aila key: Section 3.1.4, Figure 2;
  *   - Two Point (origin-termination) key: Section 3.1.5, Figure 2;
  *   - termination estimate, fixed / adaptive / real: Section 3.1.6;
+ *   - origin, origin-direction (Reis), direction-origin (Costa) and
+ *     octahedron keys: Sections 3.1.1-3.1.4, Figure 2;
  *   - stable sort of key-index pairs and the ray reorder pass: Section 3.2;
  *   - closest-hit trace: brute force over all triangles (Moller-Trumbore
  *     1997) in double precision, plus a binary BVH that must give the same
@@ -36,6 +38,14 @@
  *     keys); x is the most significant component of every triple;
  *   - the termination point p = o + t*dhat is clamped into the box by the
  *     quantiser; a non-finite estimate is replaced by 4*E;
+ *   - Reis and Costa keys of b bits give floor(b*10/32) and floor(b*8/32)
+ *     bits to the direction (the 32-bit split of Figure 2) and the rest to
+ *     the origin, each part a prefix of its own 3D Morton string;
+ *   - the octahedron key maps the direction to the square with the
+ *     octahedral parametrisation (Meyer et al. 2010), quantises both
+ *     coordinates like a position and interleaves them after the origin in
+ *     every level, with four leading zero bits removed as in the compact
+ *     Aila key (Figure 2 starts with 15 origin bits);
  *   - the length table holds fixed-point sums (units of E/2^24) in 64 bits and
  *     32-bit counts, so that accumulation is exact in any order; only rays that
  *     hit accumulate; the length of a ray is t*|d|, clamped to [0, 64*E].
@@ -47,7 +57,8 @@
 
 #define OR_MISS 0xFFFFFFFFu
 
-enum { OR_AILA = 0, OR_AILA_COMPACT = 1, OR_TWO_POINT = 2 };
+enum { OR_AILA = 0, OR_AILA_COMPACT = 1, OR_TWO_POINT = 2, OR_ORIGIN = 3, OR_REIS = 4, OR_COSTA = 5,
+       OR_OCTAHEDRON = 6 };
 enum { OR_T_FIXED = 0, OR_T_ADAPTIVE = 1, OR_T_GIVEN = 2 };
 
 /* ------------------------------------------------------------------------ */
@@ -143,6 +154,106 @@ uint64_t or_interleave(int layout, const uint32_t comp[6], uint32_t bits)
         }
     }
     return key;
+}
+
+/*
+ * Prefix of `bits` bits of the Morton string of three 32-bit components: level
+ * L holds bit 31-L of c0, c1, c2 in that order.
+ */
+uint64_t or_morton3_prefix(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t bits)
+{
+    const uint32_t c[3] = {c0, c1, c2};
+    uint64_t key = 0;
+    uint32_t taken = 0;
+    for (int L = 0; L < 32 && taken < bits; ++L)
+        for (int s = 0; s < 3 && taken < bits; ++s) {
+            key = (key << 1) | ((c[s] >> (31 - L)) & 1u);
+            taken++;
+        }
+    return key;
+}
+
+/*
+ * Octahedral parametrisation of a direction (Meyer et al. 2010): project onto
+ * the octahedron |x|+|y|+|z| = 1, fold the lower half (z < 0) over the
+ * diagonals, and map the square [-1,1]^2 to [0,1]^2.  Sign of 0 is +1.
+ */
+void or_octahedral(const float d[3], float *u, float *v)
+{
+    float ax = fabsf(d[0]), ay = fabsf(d[1]), az = fabsf(d[2]);
+    float sum = ax + ay;
+    sum = sum + az;
+    float px = 0.0f, py = 0.0f;
+    if (sum > 0.0f) {
+        px = d[0] / sum;
+        py = d[1] / sum;
+    }
+    if (d[2] < 0.0f) {
+        float sx = px >= 0.0f ? 1.0f : -1.0f;
+        float sy = py >= 0.0f ? 1.0f : -1.0f;
+        float qx = (1.0f - fabsf(py)) * sx;
+        float qy = (1.0f - fabsf(px)) * sy;
+        px = qx;
+        py = qy;
+    }
+    *u = (px + 1.0f) * 0.5f;
+    *v = (py + 1.0f) * 0.5f;
+}
+
+/*
+ * Interleaving of the other key families from their quantised components:
+ * ORIGIN reads comp[0..2]; REIS and COSTA read the origin comp[0..2] and the
+ * direction comp[3..5]; OCTAHEDRON reads the origin comp[0..2] and the two
+ * octahedral coordinates comp[3], comp[4] (already shifted right by 4).
+ */
+uint64_t or_interleave_od(int layout, const uint32_t comp[6], uint32_t bits)
+{
+    if (layout == OR_ORIGIN)
+        return or_morton3_prefix(comp[0], comp[1], comp[2], bits);
+    if (layout == OR_REIS || layout == OR_COSTA) {
+        uint32_t db = layout == OR_REIS ? (bits * 10u) / 32u : (bits * 8u) / 32u;
+        uint32_t ob = bits - db;
+        uint64_t ko = or_morton3_prefix(comp[0], comp[1], comp[2], ob);
+        uint64_t kd = or_morton3_prefix(comp[3], comp[4], comp[5], db);
+        if (layout == OR_REIS)
+            return db ? (ko << db) | kd : ko;
+        return ob ? (kd << ob) | ko : kd;
+    }
+    /* OCTAHEDRON: levels of (ox, oy, oz, u, v), direction slots of levels 0..3 dropped */
+    uint64_t key = 0;
+    uint32_t taken = 0;
+    for (int L = 0; L < 32 && taken < bits; ++L)
+        for (int s = 0; s < 5 && taken < bits; ++s) {
+            if (s >= 3 && L < 4)
+                continue;
+            key = (key << 1) | ((comp[s] >> (31 - L)) & 1u);
+            taken++;
+        }
+    return key;
+}
+
+/*
+ * Keys that read the origin and the direction only (Sections 3.1.1-3.1.4,
+ * Figure 2): ORIGIN, REIS, COSTA and OCTAHEDRON.
+ */
+uint64_t or_key_od(int layout, uint32_t bits, const float o[3], const float d[3], const float lo[3],
+                   const float hi[3])
+{
+    uint32_t qo[3], qd[3], comp[6] = {0, 0, 0, 0, 0, 0};
+    or_quantise_point(o, lo, hi, qo);
+    for (int c = 0; c < 3; ++c)
+        comp[c] = qo[c];
+    if (layout == OR_REIS || layout == OR_COSTA) {
+        or_quantise_direction(d, qd);
+        for (int c = 0; c < 3; ++c)
+            comp[3 + c] = qd[c];
+    } else if (layout == OR_OCTAHEDRON) {
+        float u, v;
+        or_octahedral(d, &u, &v);
+        comp[3] = or_quantise_unit(u) >> 4;
+        comp[4] = or_quantise_unit(v) >> 4;
+    }
+    return or_interleave_od(layout, comp, bits);
 }
 
 /* The 20-bit compacted Aila code of a ray: the length-table cell (Section 3.1.6). */
@@ -274,7 +385,8 @@ void or_compute_keys(int layout, uint32_t bits, int tsrc, float ratio, const flo
             else
                 t_est = or_table_estimate(tab_sum, tab_cnt, or_table_cell(o, d, lo, hi), tab_E);
         }
-        keys[i] = or_key(layout, bits, o, d, t_est, lo, hi);
+        keys[i] = layout >= OR_ORIGIN ? or_key_od(layout, bits, o, d, lo, hi)
+                                      : or_key(layout, bits, o, d, t_est, lo, hi);
     }
 }
 
@@ -692,4 +804,88 @@ uint32_t or_bvh_depth(const void *h)
         }
     }
     return best;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Capsule coherence measure (Section 4.3)                                   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Surface area of the capsule fitted to `m` rays: the axis joins the centroid
+ * of the origins and the centroid of the termination points; the radii are the
+ * mean distances of the origins and of the termination points from that axis
+ * (from the centroid itself when the two centroids coincide); the area is two
+ * hemispheres plus the lateral area of the cone frustum between them.  A ray's
+ * termination point is o + dhat * t with t its hit distance, or 4*E for a miss.
+ */
+static double or_capsule_area(const float *o_tmin, const float *d_tmax, const float *hits, uint32_t first,
+                              uint32_t m, float E)
+{
+    double co[3] = {0, 0, 0}, ct[3] = {0, 0, 0};
+    double po[64][3], pt[64][3];
+    for (uint32_t k = 0; k < m; ++k) {
+        uint32_t i = first + k;
+        double d[3], len = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            d[c] = d_tmax[4 * i + c];
+            len += d[c] * d[c];
+        }
+        len = sqrt(len);
+        double t = hits[4 * i + 0];
+        uint32_t tri;
+        memcpy(&tri, &hits[4 * i + 3], 4);
+        if (tri == OR_MISS || !isfinite(t))
+            t = 4.0 * (double)E;
+        for (int c = 0; c < 3; ++c) {
+            po[k][c] = o_tmin[4 * i + c];
+            pt[k][c] = po[k][c] + (len > 0.0 ? d[c] / len : 0.0) * t;
+            co[c] += po[k][c] / m;
+            ct[c] += pt[k][c] / m;
+        }
+    }
+    double a[3], a2 = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        a[c] = ct[c] - co[c];
+        a2 += a[c] * a[c];
+    }
+    double ro = 0.0, rt = 0.0;
+    for (int which = 0; which < 2; ++which)
+        for (uint32_t k = 0; k < m; ++k) {
+            const double *x = which == 0 ? po[k] : pt[k];
+            double v[3], proj = 0.0, dist2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                v[c] = x[c] - co[c];
+                proj += v[c] * a[c];
+            }
+            proj = a2 > 0.0 ? proj / a2 : 0.0;
+            for (int c = 0; c < 3; ++c) {
+                double w = v[c] - proj * a[c];
+                dist2 += w * w;
+            }
+            if (which == 0)
+                ro += sqrt(dist2) / m;
+            else
+                rt += sqrt(dist2) / m;
+        }
+    const double pi = 3.14159265358979323846;
+    double h = sqrt(a2);
+    return 2.0 * pi * ro * ro + 2.0 * pi * rt * rt + pi * (ro + rt) * sqrt(h * h + (ro - rt) * (ro - rt));
+}
+
+/*
+ * Capsule areas of the consecutive subsets of `subset` rays (1..64); a tail
+ * shorter than `subset` is ignored unless n < subset.  out receives
+ * max(1, n / subset) values for n > 0; returns their count.
+ */
+uint32_t or_capsule_areas(const float *o_tmin, const float *d_tmax, const float *hits, uint32_t n,
+                          uint32_t subset, float E, double *out)
+{
+    if (n == 0 || subset == 0 || subset > 64)
+        return 0;
+    uint32_t groups = n < subset ? 1 : n / subset;
+    for (uint32_t g = 0; g < groups; ++g) {
+        uint32_t m = n < subset ? n : subset;
+        out[g] = or_capsule_area(o_tmin, d_tmax, hits, g * subset, m, E);
+    }
+    return groups;
 }

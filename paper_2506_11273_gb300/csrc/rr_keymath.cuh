@@ -85,6 +85,65 @@ __device__ __forceinline__ uint64_t interleave_compact_64(const uint32_t c[6]) {
     return ((uint64_t)head << 55) | (body << 1) | (uint64_t)((c[0] >> 19) & 1u);  // + level 12, x
 }
 
+// Spreads the low 21 bits of x so that bit i lands on bit 3i.
+__device__ __forceinline__ uint64_t spread3_21(uint64_t x) {
+    x &= 0x1FFFFFull;
+    x = (x | (x << 32)) & 0x1F00000000FFFFull;
+    x = (x | (x << 16)) & 0x1F0000FF0000FFull;
+    x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+    x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+// First 64 bits of the Morton string of three components (level L holds bit
+// 31-L of c0, c1, c2): levels 0..20 and the first slot of level 21.
+__device__ __forceinline__ uint64_t morton3_64(uint32_t c0, uint32_t c1, uint32_t c2) {
+    const uint64_t m = (spread3_21(c0 >> 11) << 2) | (spread3_21(c1 >> 11) << 1) | spread3_21(c2 >> 11);
+    return (m << 1) | ((c0 >> 10) & 1u);
+}
+
+// The first k bits of a 64-bit string (k = 0..64).
+__device__ __forceinline__ uint64_t prefix64(uint64_t s, uint32_t k) { return k ? s >> (64 - k) : 0ull; }
+
+// Spreads the low 10 bits of x so that bit i lands on bit 5i.
+__device__ __forceinline__ uint64_t spread5_10(uint32_t x) {
+    uint64_t r = 0;
+#pragma unroll
+    for (int i = 0; i < 10; ++i) r |= (uint64_t)((x >> i) & 1u) << (5 * i);
+    return r;
+}
+
+// Octahedral parametrisation of a direction (Meyer et al. 2010) in [0,1]^2.
+__device__ __forceinline__ void octahedral(float dx, float dy, float dz, float &u, float &v) {
+    const float sum = __fadd_rn(__fadd_rn(fabsf(dx), fabsf(dy)), fabsf(dz));
+    float px = 0.0f, py = 0.0f;
+    if (sum > 0.0f) {
+        px = __fdiv_rn(dx, sum);
+        py = __fdiv_rn(dy, sum);
+    }
+    if (dz < 0.0f) {
+        const float sx = px >= 0.0f ? 1.0f : -1.0f, sy = py >= 0.0f ? 1.0f : -1.0f;
+        const float qx = __fmul_rn(__fsub_rn(1.0f, fabsf(py)), sx);
+        const float qy = __fmul_rn(__fsub_rn(1.0f, fabsf(px)), sy);
+        px = qx;
+        py = qy;
+    }
+    u = __fmul_rn(__fadd_rn(px, 1.0f), 0.5f);
+    v = __fmul_rn(__fadd_rn(py, 1.0f), 0.5f);
+}
+
+// Octahedron key string: levels 0..3 hold the origin only, later levels the
+// origin and the two octahedral coordinates (c[3], c[4], each the quantised
+// coordinate shifted right by 4).  First 64 bits: 12 + 5*10 + 2.
+__device__ __forceinline__ uint64_t interleave_octa_64(const uint32_t c[5]) {
+    const uint64_t head = (spread3_21(c[0] >> 28) << 2) | (spread3_21(c[1] >> 28) << 1) | spread3_21(c[2] >> 28);
+    uint64_t body = 0;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) body |= spread5_10((c[s] >> 18) & 0x3FFu) << (4 - s);  // levels 4..13
+    return (head << 52) | (body << 2) | ((uint64_t)((c[0] >> 17) & 1u) << 1) | (uint64_t)((c[1] >> 17) & 1u);
+}
+
 // Quantised origin and direction of a ray (direction normalised, mapped to [0,1]).
 __device__ __forceinline__ void quantise_ray(const QuantFrame &f, float4 o, float4 d, uint32_t qo[3],
                                              uint32_t qd[3], float dh[3]) {

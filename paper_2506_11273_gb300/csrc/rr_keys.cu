@@ -57,9 +57,26 @@ __global__ void __launch_bounds__(256) key_kernel(KeyArgs a) {
         c[4] = quantise_coord(f, 1, __fadd_rn(o.y, __fmul_rn(dh[1], t)));
         c[5] = quantise_coord(f, 2, __fadd_rn(o.z, __fmul_rn(dh[2], t)));
         key64 = interleave6_64(c);
-    } else {
+    } else if (LAYOUT == RR_KEY_AILA || LAYOUT == RR_KEY_AILA_COMPACT) {
         uint32_t c[6] = {qo[0], qo[1], qo[2], qd[0] >> 3, qd[1] >> 3, qd[2] >> 3};
         key64 = LAYOUT == RR_KEY_AILA ? interleave6_64(c) : interleave_compact_64(c);
+    } else if (LAYOUT == RR_KEY_ORIGIN) {
+        key64 = morton3_64(qo[0], qo[1], qo[2]);
+    } else if (LAYOUT == RR_KEY_REIS || LAYOUT == RR_KEY_COSTA) {
+        // two prefixes of their own Morton strings; the 32-bit split of Figure 2
+        // (22 + 10 and 8 + 24) scaled to `bits`
+        const uint32_t db = LAYOUT == RR_KEY_REIS ? (a.bits * 10u) / 32u : (a.bits * 8u) / 32u;
+        const uint32_t ob = a.bits - db;
+        const uint64_t ko = prefix64(morton3_64(qo[0], qo[1], qo[2]), ob);
+        const uint64_t kd = prefix64(morton3_64(qd[0], qd[1], qd[2]), db);
+        const uint64_t key = LAYOUT == RR_KEY_REIS ? (db ? (ko << db) | kd : ko) : (ob ? (kd << ob) | ko : kd);
+        static_cast<KeyT *>(a.keys)[i] = (KeyT)key;
+        return;
+    } else {
+        float u, v;
+        octahedral(d.x, d.y, d.z, u, v);
+        const uint32_t c[5] = {qo[0], qo[1], qo[2], quantise_unit(u) >> 4, quantise_unit(v) >> 4};
+        key64 = interleave_octa_64(c);
     }
     uint64_t key = key64 >> (64 - a.bits);
     static_cast<KeyT *>(a.keys)[i] = (KeyT)key;
@@ -147,7 +164,7 @@ using namespace rr;
 extern "C" rr_status rr_compute_keys(const float *o_tmin, const float *d_tmax, uint32_t n,
                                      const rr_key_params *p, void *keys_out, void *stream) {
     if (!p) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: params is NULL");
-    if (p->layout > RR_KEY_TWO_POINT) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: bad layout");
+    if (p->layout > RR_KEY_OCTAHEDRON) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: bad layout");
     if (p->bits < 1 || p->bits > 64) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: bits not in 1..64");
     if (p->layout == RR_KEY_TWO_POINT && p->t_source > RR_T_GIVEN)
         return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: bad t_source");
@@ -178,6 +195,14 @@ extern "C" rr_status rr_compute_keys(const float *o_tmin, const float *d_tmax, u
         launch_keys<RR_KEY_AILA, 0>(a, wide, s);
     } else if (p->layout == RR_KEY_AILA_COMPACT) {
         launch_keys<RR_KEY_AILA_COMPACT, 0>(a, wide, s);
+    } else if (p->layout == RR_KEY_ORIGIN) {
+        launch_keys<RR_KEY_ORIGIN, 0>(a, wide, s);
+    } else if (p->layout == RR_KEY_REIS) {
+        launch_keys<RR_KEY_REIS, 0>(a, wide, s);
+    } else if (p->layout == RR_KEY_COSTA) {
+        launch_keys<RR_KEY_COSTA, 0>(a, wide, s);
+    } else if (p->layout == RR_KEY_OCTAHEDRON) {
+        launch_keys<RR_KEY_OCTAHEDRON, 0>(a, wide, s);
     } else if (p->t_source == RR_T_FIXED) {
         if (!std::isfinite(p->ratio)) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: ratio not finite");
         launch_keys<RR_KEY_TWO_POINT, RR_T_FIXED>(a, wide, s);

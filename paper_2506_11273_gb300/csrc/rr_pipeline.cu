@@ -31,7 +31,7 @@ extern "C" rr_status rr_pipeline_create(const rr_bvh *bvh, uint32_t max_n, const
     if (!out || !bvh || !params) return fail(RR_ERR_INVALID_ARG, "rr_pipeline_create: NULL argument");
     *out = nullptr;
     if (max_n == 0) return fail(RR_ERR_INVALID_ARG, "rr_pipeline_create: max_n is 0");
-    if (params->bits < 1 || params->bits > 64 || params->layout > RR_KEY_TWO_POINT)
+    if (params->bits < 1 || params->bits > 64 || params->layout > RR_KEY_OCTAHEDRON)
         return fail(RR_ERR_INVALID_ARG, "rr_pipeline_create: bad key params");
     size_t ws = 0;
     rr_status st = rr_sort_workspace_size(max_n, params->bits, radix_bits, &ws);

@@ -26,6 +26,7 @@ _lock = threading.Lock()
 _lib = None
 
 RR_KEY_AILA, RR_KEY_AILA_COMPACT, RR_KEY_TWO_POINT = 0, 1, 2
+RR_KEY_ORIGIN, RR_KEY_REIS, RR_KEY_COSTA, RR_KEY_OCTAHEDRON = 3, 4, 5, 6
 RR_T_FIXED, RR_T_ADAPTIVE, RR_T_GIVEN = 0, 1, 2
 RR_DEVERR_LOOKBACK_TIMEOUT = 0x1
 RR_DEVERR_TRACE_STACK = 0x2
@@ -44,6 +45,7 @@ EXPORTS = [
     "rr_length_table_write", "rr_length_table_destroy", "rr_pipeline_create",
     "rr_pipeline_destroy", "rr_pipeline_run", "rr_pipeline_run_host", "rr_device_error",
     "rr_status_string", "rr_last_error_message", "rr_kernel_launch_count", "rr_sort_noalloc",
+    "rr_coherence_capsule",
 ]
 
 
@@ -96,6 +98,7 @@ def lib():
             L.rr_pipeline_destroy.argtypes = [vp]
             L.rr_pipeline_run.argtypes = [vp, vp, vp, vp, u32, vp, vp, vp]
             L.rr_pipeline_run_host.argtypes = [vp, vp, vp, vp, u32, vp, vp, vp]
+            L.rr_coherence_capsule.argtypes = [vp, vp, vp, u32, u32, C.c_float, vp, vp]
             L.rr_device_error.argtypes = [C.POINTER(C.c_uint32)]
             L.rr_status_string.argtypes = [i32]
             L.rr_status_string.restype = C.c_char_p
@@ -343,6 +346,21 @@ class Pipeline:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- coherence measure
+
+def rr_coherence_capsule(o_tmin, d_tmax, hits, E: float, subset: int = 64, areas_out=None,
+                         n: int | None = None, stream=None):
+    """Capsule area of every run of `subset` consecutive rays (Section 4.3)."""
+    n = o_tmin.shape[0] if n is None else n
+    groups = 1 if n < subset else n // subset
+    if areas_out is None:
+        areas_out = torch.empty(groups, dtype=torch.float32, device=o_tmin.device)
+    _check(lib().rr_coherence_capsule(_ptr(o_tmin), _ptr(d_tmax), _ptr(hits), n, subset,
+                                      float(np.float32(E)), _ptr(areas_out), _stream(stream)),
+           "rr_coherence_capsule")
+    return areas_out
 
 
 # ---------------------------------------------------------------- diagnostics

@@ -15,7 +15,10 @@ from paper_2506_11273_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 LAYOUTS = {"aila": (rr.RR_KEY_AILA, oracle.AILA), "compact": (rr.RR_KEY_AILA_COMPACT, oracle.AILA_COMPACT),
-           "two_point": (rr.RR_KEY_TWO_POINT, oracle.TWO_POINT)}
+           "two_point": (rr.RR_KEY_TWO_POINT, oracle.TWO_POINT), "origin": (rr.RR_KEY_ORIGIN, oracle.ORIGIN),
+           "reis": (rr.RR_KEY_REIS, oracle.REIS), "costa": (rr.RR_KEY_COSTA, oracle.COSTA),
+           "octahedron": (rr.RR_KEY_OCTAHEDRON, oracle.OCTAHEDRON)}
+ALL_LAYOUTS = list(LAYOUTS)
 TSRC = {"fixed": (rr.RR_T_FIXED, oracle.T_FIXED), "adaptive": (rr.RR_T_ADAPTIVE, oracle.T_ADAPTIVE),
         "given": (rr.RR_T_GIVEN, oracle.T_GIVEN)}
 
@@ -51,8 +54,8 @@ def assert_no_device_error():
 
 # ------------------------------------------------------------------ keys
 
-@pytest.mark.parametrize("name", ["aila", "compact", "two_point"])
-@pytest.mark.parametrize("bits", [1, 16, 20, 31, 32, 33, 48, 63, 64])
+@pytest.mark.parametrize("name", ALL_LAYOUTS)
+@pytest.mark.parametrize("bits", [1, 3, 4, 16, 20, 31, 32, 33, 48, 63, 64])
 def test_keys_match_oracle(soup, name, bits):
     tris, rays, lo, hi = soup
     g, o = LAYOUTS[name]
@@ -125,7 +128,7 @@ def test_keys_edge_values_and_sizes(n):
     boxes = [(np.zeros(3, np.float32), np.ones(3, np.float32)),
              (np.array([0, 0.5, 0], np.float32), np.array([1, 0.5, 2], np.float32))]  # flat axis
     for lo, hi in boxes:
-        for name in ("aila", "compact", "two_point"):
+        for name in ALL_LAYOUTS:
             g, o = LAYOUTS[name]
             for bits in (32, 64):
                 k_gpu = gpu_keys(rays, g, bits, lo, hi)

@@ -261,3 +261,28 @@ def test_trace_accumulate_equals_trace_then_accumulate():
     s2, c2 = t2.read()
     assert np.array_equal(s1, s2) and np.array_equal(c1, c2)
     assert int(c2.sum()) > (1 << 20)
+
+
+def test_capsule_coherence_matches_oracle_and_ranks_orders():
+    """Per-run capsule areas match the oracle (fp32 vs binary64), and sorting by
+    the Two Point key lowers the mean area (Section 4.3's measure)."""
+    tris = W.scene_box_soup(seed=1)
+    rays = W.rays_box_soup(tris, n=65536, seed=5)
+    lo, hi = W.scene_aabb(tris)
+    E = float(oracle.largest_extent(lo, hi))
+    hits, _ = oracle.BVH(tris).trace(rays.o_tmin, rays.d_tmax)
+    o, d, _ = rr.to_device_rays(rays)
+    h = torch.from_numpy(hits).cuda()
+    g = rr.rr_coherence_capsule(o, d, h, E).cpu().numpy()
+    ref = oracle.capsule_areas(rays.o_tmin, rays.d_tmax, hits, E)
+    assert g.shape == ref.shape == (1024,)
+    assert np.allclose(g, ref, rtol=2e-4, atol=1e-6)
+    for subset, n in ((64, 100), (17, 1000), (64, 5)):
+        gs = rr.rr_coherence_capsule(o[:n].contiguous(), d[:n].contiguous(), h[:n].contiguous(), E,
+                                     subset=subset).cpu().numpy()
+        rs = oracle.capsule_areas(rays.o_tmin[:n], rays.d_tmax[:n], hits[:n], E, subset=subset)
+        assert np.allclose(gs, rs, rtol=2e-4, atol=1e-6)
+    keys = oracle.compute_keys(oracle.TWO_POINT, 64, rays.o_tmin, rays.d_tmax, lo, hi)
+    perm, _ = oracle.stable_sort(keys)
+    sorted_area = oracle.capsule_areas(rays.o_tmin[perm], rays.d_tmax[perm], hits[perm], E).mean()
+    assert sorted_area < 0.5 * ref.mean()

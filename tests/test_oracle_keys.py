@@ -45,7 +45,8 @@ LAYOUTS = {"Aila": oracle.AILA, "Aila_Compact": oracle.AILA_COMPACT, "Two_Point"
 
 def test_golden_rows_have_32_bits():
     rows = figure2_rows()
-    assert set(rows) == {"Aila", "Aila_Compact", "Two_Point", "Compact_20"}
+    assert set(rows) == {"Aila", "Aila_Compact", "Two_Point", "Compact_20", "Origin", "Reis", "Costa",
+                         "Octahedron"}
     for name, seq in rows.items():
         assert len(seq) == (20 if name == "Compact_20" else 32), name
 
@@ -256,3 +257,100 @@ def test_table_cell_is_compact_prefix():
         k32 = oracle.key(oracle.AILA_COMPACT, 32, o, d, 0.0, LO, HI)
         assert cell == k32 >> 12
         assert cell < (1 << 20)
+
+
+# ------------------------------------------------------------- other key families
+
+OD_LAYOUTS = {"Origin": oracle.ORIGIN, "Reis": oracle.REIS, "Costa": oracle.COSTA,
+              "Octahedron": oracle.OCTAHEDRON}
+
+
+def _od_comp(layout, origin, direction):
+    """Component vector of or_interleave_od with `origin` / `direction` bits set."""
+    if layout == oracle.OCTAHEDRON:
+        return [origin] * 3 + [direction >> 4] * 2
+    return [origin] * 3 + [direction] * 3
+
+
+@pytest.mark.parametrize("name", ["Origin", "Reis", "Costa", "Octahedron"])
+def test_figure2_class_masks_other_families(name):
+    seq = figure2_rows()[name]
+    masks = masks_from_row(seq)
+    layout = OD_LAYOUTS[name]
+    ones = 0xFFFFFFFF
+    assert oracle.interleave_od(layout, _od_comp(layout, ones, 0), 32) == masks["o"]
+    if "d" in masks:
+        assert oracle.interleave_od(layout, _od_comp(layout, 0, ones), 32) == masks["d"]
+        assert oracle.interleave_od(layout, _od_comp(layout, ones, ones), 32) == 0xFFFFFFFF
+
+
+@pytest.mark.parametrize("name", ["Origin", "Reis", "Costa", "Octahedron"])
+def test_figure2_single_bit_positions_other_families(name):
+    """The k-th o (d) bit of a row is axis k mod 3 (mod 2 for the octahedral
+    u, v) at level k div 3 (div 2) of its component; octahedral direction bits
+    start at level 4 (four leading zero bits)."""
+    seq = figure2_rows()[name]
+    layout = OD_LAYOUTS[name]
+    count = {}
+    for pos, c in enumerate(seq):
+        k = count.get(c, 0)
+        count[c] = k + 1
+        comp = [0] * 6
+        if c == "o":
+            comp[k % 3] = 1 << (31 - k // 3)
+        elif layout == oracle.OCTAHEDRON:
+            comp[3 + k % 2] = 1 << (31 - (k // 2 + 4))
+        else:
+            comp[3 + k % 3] = 1 << (31 - k // 3)
+        assert oracle.interleave_od(layout, comp, 32) == 1 << (31 - pos), (name, pos, c)
+
+
+def test_origin_key_is_textbook_morton():
+    rng = np.random.default_rng(21)
+    for _ in range(200):
+        q = rng.integers(0, 2**32, size=3, dtype=np.uint64).astype(np.uint32)
+        k30 = oracle.interleave_od(oracle.ORIGIN, [q[0], q[1], q[2]], 30)
+        assert k30 == morton30(int(q[0] >> 22), int(q[1] >> 22), int(q[2] >> 22))
+
+
+def test_reis_and_costa_split_origin_and_direction():
+    """32 bits: Reis = 22 origin + 10 direction bits, Costa = 8 direction + 24 origin."""
+    rng = np.random.default_rng(22)
+    for _ in range(100):
+        c = rng.integers(0, 2**32, size=6, dtype=np.uint64).astype(np.uint32)
+        ko22 = oracle.morton3_prefix(c[0], c[1], c[2], 22)
+        kd10 = oracle.morton3_prefix(c[3], c[4], c[5], 10)
+        assert oracle.interleave_od(oracle.REIS, c, 32) == (ko22 << 10) | kd10
+        kd8 = oracle.morton3_prefix(c[3], c[4], c[5], 8)
+        ko24 = oracle.morton3_prefix(c[0], c[1], c[2], 24)
+        assert oracle.interleave_od(oracle.COSTA, c, 32) == (kd8 << 24) | ko24
+
+
+def test_octahedral_closed_forms():
+    """Poles, equator points and the folded lower hemisphere (Meyer et al. 2010)."""
+    cases = {(0, 0, 1): (0.5, 0.5), (0, 0, -1): (1.0, 1.0), (1, 0, 0): (1.0, 0.5), (-1, 0, 0): (0.0, 0.5),
+             (0, 1, 0): (0.5, 1.0), (0, -1, 0): (0.5, 0.0), (1, 1, 0): (0.75, 0.75),
+             (1, 0, -1): (1.0, 0.75), (-1, 0, -1): (0.0, 0.75), (0, 0, 0): (0.5, 0.5)}
+    for d, (u, v) in cases.items():
+        uu, vv = oracle.octahedral(np.array(d, np.float32))
+        assert (float(uu), float(vv)) == (u, v), d
+    # the map is onto the square and scale-free
+    rng = np.random.default_rng(23)
+    for _ in range(200):
+        d = rng.normal(size=3).astype(np.float32)
+        u, v = oracle.octahedral(d)
+        assert 0.0 <= u <= 1.0 and 0.0 <= v <= 1.0
+        u2, v2 = oracle.octahedral(d * np.float32(4.0))
+        assert (u, v) == (u2, v2)
+
+
+def test_other_family_keys_from_rays_use_the_quantisers():
+    o = np.array([0.25, 0.5, 0.75], np.float32)
+    d = np.array([0, 0, 1], np.float32)
+    qo = oracle.quantise_point(o, LO, HI)
+    qd = oracle.quantise_direction(d)
+    assert oracle.key_od(oracle.ORIGIN, 64, o, d, LO, HI) == oracle.interleave_od(oracle.ORIGIN, qo, 64)
+    assert oracle.key_od(oracle.REIS, 48, o, d, LO, HI) == oracle.interleave_od(oracle.REIS, list(qo) + list(qd), 48)
+    u, v = oracle.octahedral(d)
+    comp = list(qo) + [oracle.quantise_unit(u) >> 4, oracle.quantise_unit(v) >> 4]
+    assert oracle.key_od(oracle.OCTAHEDRON, 64, o, d, LO, HI) == oracle.interleave_od(oracle.OCTAHEDRON, comp, 64)

@@ -262,3 +262,69 @@ def test_adaptive_key_uses_table_estimate():
     assert np.array_equal(ka, kg)
     # and the estimates moved away from the dummy value where rays hit
     assert np.mean(t_est != np.float32(0.25) * E) > 0.5
+
+
+# ------------------------------------------------------------------ capsule coherence measure
+
+def _rays_from(o, d, t):
+    n = len(o)
+    o_tmin = np.zeros((n, 4), np.float32)
+    d_tmax = np.zeros((n, 4), np.float32)
+    hits = np.zeros((n, 4), np.float32)
+    o_tmin[:, :3] = o
+    d_tmax[:, :3] = d
+    d_tmax[:, 3] = np.inf
+    hits[:, 0] = t
+    hits[:, 3] = np.zeros(n, np.uint32).view(np.float32)
+    return o_tmin, d_tmax, hits
+
+
+def test_capsule_of_parallel_rays_is_a_cylinder():
+    """64 rays on a circle of radius r, all along +z with length h: hemispheres
+    of radius r at both ends and a cylinder between, area 4*pi*r^2 + 2*pi*r*h."""
+    r, h = 0.5, 3.0
+    ang = np.arange(64) * 2 * np.pi / 64
+    o = np.stack([r * np.cos(ang), r * np.sin(ang), np.zeros(64)], 1)
+    d = np.tile([0, 0, 1.0], (64, 1))
+    ot, dt, hits = _rays_from(o, d, np.full(64, h))
+    a = oracle.capsule_areas(ot, dt, hits, E=10.0)
+    assert a.shape == (1,)
+    r_meas = np.mean(np.hypot(o[:, 0].astype(np.float32), o[:, 1].astype(np.float32)))
+    assert abs(a[0] - (4 * np.pi * r_meas ** 2 + 2 * np.pi * r_meas * h)) < 1e-6 * a[0]
+
+
+def test_capsule_of_a_cone_and_a_point():
+    """Rays from one point fanning out to a circle: r_o = 0, r_t = R: the area is
+    a hemisphere of radius R plus the cone's lateral area pi*R*sqrt(h^2 + R^2)."""
+    R, h = 2.0, 5.0
+    ang = np.arange(64) * 2 * np.pi / 64
+    tgt = np.stack([R * np.cos(ang), R * np.sin(ang), np.full(64, h)], 1)
+    o = np.zeros((64, 3))
+    d = tgt / np.linalg.norm(tgt, axis=1, keepdims=True)
+    ot, dt, hits = _rays_from(o, d, np.linalg.norm(tgt, axis=1))
+    a = oracle.capsule_areas(ot, dt, hits, E=10.0)[0]
+    assert abs(a - (2 * np.pi * R * R + np.pi * R * np.sqrt(h * h + R * R))) < 1e-4 * a
+
+
+def test_capsule_subsets_and_misses():
+    rng = np.random.default_rng(4)
+    o = rng.random((200, 3))
+    d = rng.normal(size=(200, 3))
+    ot, dt, hits = _rays_from(o, d, rng.random(200))
+    a = oracle.capsule_areas(ot, dt, hits, E=1.0)
+    assert a.shape == (3,)  # 200 // 64; the tail of 8 is ignored
+    for g in range(3):
+        sl = slice(64 * g, 64 * g + 64)
+        assert a[g] == oracle.capsule_areas(ot[sl], dt[sl], hits[sl], E=1.0)[0]
+    # a miss terminates at 4*E
+    h2 = hits.copy()
+    h2[:64, 3] = np.full(64, oracle.MISS, np.uint32).view(np.float32)
+    h3 = hits.copy()
+    h3[:64, 0] = 4.0
+    assert oracle.capsule_areas(ot, dt, h2, E=1.0)[0] == oracle.capsule_areas(ot, dt, h3, E=1.0)[0]
+    # coherent rays give a smaller capsule than the same rays shuffled
+    o_c = np.repeat(rng.random((4, 3)), 64, axis=0) + rng.random((256, 3)) * 0.01
+    d_c = np.repeat(rng.normal(size=(4, 3)), 64, axis=0) + rng.normal(size=(256, 3)) * 0.01
+    ot, dt, hits = _rays_from(o_c, d_c, np.full(256, 0.5))
+    p = rng.permutation(256)
+    assert oracle.capsule_areas(ot, dt, hits, 1.0).mean() < oracle.capsule_areas(ot[p], dt[p], hits[p], 1.0).mean()
