@@ -214,22 +214,32 @@ def run_ours(args):
     params_tp = rr.key_params(rr.RR_KEY_TWO_POINT, KEY_BITS, lo, hi, t_source=rr.RR_T_ADAPTIVE, table=table)
     params_aila = rr.key_params(rr.RR_KEY_AILA, KEY_BITS, lo, hi)
 
-    def make_step(B, params, accumulate, bits=KEY_BITS):
+    def make_step(B, params, accumulate, bits=KEY_BITS, sort="global", segment=2048, reorder="gather"):
+        """One bounce: key -> sort (global onesweep, or local per segment) ->
+        reorder (gather the SoA, or trace through the permutation) -> trace."""
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
         keys, ws = (B["keys"], B["ws"]) if bits > 32 else (B["keys32"], B["ws32"])
+        tbl = table if accumulate else None
 
         def step():
             ev[0].record(stream)
             rr.rr_compute_keys(B["o"], B["d"], params, keys)
             ev[1].record(stream)
-            rr.rr_sort(keys, None, B["perm"], B["n"], bits, RADIX_BITS, ws)
-            ev[2].record(stream)
-            rr.rr_permute(B["o"], B["d"], B["p"], B["perm"], B["so"], B["sd"], B["sp"])
-            ev[3].record(stream)
-            if accumulate:  # trace and length-table update in one kernel
-                rr.rr_trace_accumulate(bvh, B["so"], B["sd"], B["hits"], table)
+            if sort == "global":
+                rr.rr_sort(keys, None, B["perm"], B["n"], bits, RADIX_BITS, ws)
             else:
-                rr.rr_trace(bvh, B["so"], B["sd"], B["hits"])
+                rr.rr_sort_segments(keys, None, B["perm"], B["n"], bits, segment)
+            ev[2].record(stream)
+            if reorder == "gather":
+                rr.rr_permute(B["o"], B["d"], B["p"], B["perm"], B["so"], B["sd"], B["sp"])
+                ev[3].record(stream)
+                if accumulate:  # trace and length-table update in one kernel
+                    rr.rr_trace_accumulate(bvh, B["so"], B["sd"], B["hits"], table)
+                else:
+                    rr.rr_trace(bvh, B["so"], B["sd"], B["hits"])
+            else:  # indirect access: the trace reads the rays through perm
+                ev[3].record(stream)
+                rr.rr_trace_ex(bvh, B["o"], B["d"], B["hits"], order=B["perm"], table=tbl)
             ev[4].record(stream)
             ev[5].record(stream)
 
@@ -308,6 +318,28 @@ def run_ours(args):
     extra["two_point_32bit_mrays"] = round(n * max(3, args.steps // 2) / (tot_32 * 1e-3) / 1e6, 2)
     extra["two_point_32bit_phases_ms"] = {k: round(float(v), 4) for k, v in
                                           zip(["key", "sort", "gather", "trace"], np.median(np.array(ph_32), axis=0)[:4])}
+
+    # cheaper reorderings of the same bounce (local sort, indirect access)
+    variants = {}
+    kv = max(3, args.steps // 2)
+    for name, kw in [("global64_indirect", dict(params=params_tp, accumulate=True, reorder="indirect")),
+                     ("global32_indirect", dict(params=params_tp32, accumulate=True, bits=32, reorder="indirect")),
+                     ("local1024_indirect", dict(params=params_tp, accumulate=True, sort="segment", segment=1024,
+                                                 reorder="indirect")),
+                     ("local2048_indirect", dict(params=params_tp, accumulate=True, sort="segment", segment=2048,
+                                                 reorder="indirect")),
+                     ("local4096_indirect", dict(params=params_tp, accumulate=True, sort="segment", segment=4096,
+                                                 reorder="indirect")),
+                     ("local4096_gather", dict(params=params_tp, accumulate=True, sort="segment", segment=4096))]:
+        st_v, pf_v = make_step(B, **kw)
+        tot_v, _, ph_v = timed(st_v, kv, 3, pf_v)
+        med = np.median(np.array(ph_v), axis=0)
+        variants[name] = {"mrays": round(n * kv / (tot_v * 1e-3) / 1e6, 2),
+                          "phases_ms": {k: round(float(v), 4) for k, v in
+                                        zip(["key", "sort", "gather", "trace"], med[:4])}}
+    extra["reorder_variants"] = variants
+    if rr.rr_device_error() != 0:
+        raise RuntimeError("device error flag set during the reorder variants")
 
     if not args.no_extra:
         per_bounce = []

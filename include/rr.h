@@ -57,6 +57,7 @@ typedef enum {
 /* Device error flags accumulated in the per-device error word. */
 #define RR_DEVERR_LOOKBACK_TIMEOUT 0x1u
 #define RR_DEVERR_TRACE_STACK 0x2u
+#define RR_DEVERR_BAD_INDEX 0x4u /* an index buffer entry was >= n; that entry was skipped */
 
 /* Sorting-key layouts (Section 3.1, Figure 2). */
 typedef enum {
@@ -159,6 +160,19 @@ rr_status rr_sort(const void *keys_in, void *keys_out, uint32_t *perm_out, uint3
                   void *stream);
 
 /*
+ * rr_sort_segments - local (block-wise) sort, Section 3.2: the keys are cut
+ * into consecutive segments of `segment` keys (256, 512, 1024, 2048 or 4096;
+ * the last segment may be shorter) and each segment is sorted stably by its
+ * low `bits` bits on its own, in on-chip memory.  perm_out[i] (device, n
+ * uint32) is a global index: segment s holds a permutation of its own range
+ * [s * segment, min(n, (s + 1) * segment)).  keys_out (device or NULL)
+ * receives the keys in that order.  Same key types and alignment rules as
+ * rr_sort; needs no workspace; one kernel.  n < 2^30.
+ */
+rr_status rr_sort_segments(const void *keys_in, void *keys_out, uint32_t *perm_out, uint32_t n, uint32_t bits,
+                           uint32_t segment, void *stream);
+
+/*
  * rr_sort_noalloc - rr_sort for callers that cannot allocate device memory.
  * The paper has no counterpart: it exists for integration, not for the method.
  *
@@ -236,6 +250,32 @@ rr_status rr_trace(const rr_bvh *bvh, const float *o_tmin, const float *d_tmax, 
  */
 rr_status rr_trace_accumulate(const rr_bvh *bvh, const float *o_tmin, const float *d_tmax,
                               uint32_t n, float *hits_out, rr_length_table *table, void *stream);
+
+/* Flags of rr_trace_ex. */
+#define RR_TRACE_ANY_HIT 0x1u /* shadow rays: stop at the first hit inside (tmin, tmax) */
+
+/*
+ * rr_trace_ex - rr_trace with two options of the reordering study.
+ *
+ * order (device, n uint32, or NULL): indirect access.  Work position k traces
+ * ray order[k] and writes its hit to hits_out[order[k]], so a permutation from
+ * rr_sort sets which rays share a warp without the rays being gathered first,
+ * and the hits come back in the order of the input rays (Section 5, the
+ * indirect ray access of the CUDA trace kernel).  order must be a permutation
+ * of [0, n): an entry >= n is skipped and sets RR_DEVERR_BAD_INDEX; a repeated
+ * entry traces that ray twice.  NULL: position k traces ray k (rr_trace).
+ *
+ * flags: RR_TRACE_ANY_HIT ends each ray at the first triangle it meets inside
+ * (tmin, tmax), as an any-hit kernel for shadow rays does (Section 4, shadow
+ * rays); the hit record describes that triangle (its t, barycentrics and id),
+ * and a miss is reported as in rr_trace.  Which triangle is found first
+ * depends on the traversal order; whether one is found does not.
+ *
+ * table: NULL, or a length table to update as rr_trace_accumulate does (not
+ * with RR_TRACE_ANY_HIT: RR_ERR_INVALID_ARG).
+ */
+rr_status rr_trace_ex(const rr_bvh *bvh, const float *o_tmin, const float *d_tmax, const uint32_t *order,
+                      uint32_t n, float *hits_out, uint32_t flags, rr_length_table *table, void *stream);
 
 /* ---------------------------------------------------------------- ray-length table */
 

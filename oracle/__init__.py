@@ -83,6 +83,8 @@ def lib():
             L.or_capsule_areas.argtypes = [_f32p, _f32p, _f32p, C.c_uint32, C.c_uint32, C.c_float, _f64p]
             L.or_stable_sort.restype = C.c_int
             L.or_stable_sort.argtypes = [_u64p, C.c_uint32, _u32p, _u64p]
+            L.or_segment_sort.restype = C.c_int
+            L.or_segment_sort.argtypes = [_u64p, C.c_uint32, C.c_uint32, _u32p]
             L.or_permute.argtypes = [_f32p, _f32p, _u32p, _u32p, C.c_uint32, _f32p, _f32p, _u32p]
             L.or_ray_triangle.restype = C.c_int
             L.or_ray_triangle.argtypes = [_f64p, _f64p, _f32p, C.POINTER(C.c_double),
@@ -221,6 +223,15 @@ def stable_sort(keys):
     if lib().or_stable_sort(keys, n, perm, sk) != 0:
         raise MemoryError("oracle sort")
     return perm, sk
+
+
+def segment_sort(keys, segment: int):
+    """Stable sort inside each run of `segment` consecutive keys (Section 3.2)."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    perm = np.zeros(keys.shape[0], np.uint32)
+    if lib().or_segment_sort(keys, keys.shape[0], segment, perm) != 0:
+        raise ValueError("oracle segment sort")
+    return perm
 
 
 def permute(o_tmin, d_tmax, payload, perm):

@@ -428,6 +428,28 @@ int or_stable_sort(const uint64_t *keys, uint32_t n, uint32_t *perm, uint64_t *s
     return 0;
 }
 
+/*
+ * Local (block-wise) sort, Section 3.2: the rays are cut into consecutive
+ * segments of `segment` rays (the last one may be shorter) and each segment is
+ * sorted stably on its own.  perm holds global ray indices; segment s occupies
+ * perm[s*segment ...] and holds exactly the indices of its own range.
+ */
+int or_segment_sort(const uint64_t *keys, uint32_t n, uint32_t segment, uint32_t *perm)
+{
+    if (segment == 0)
+        return 1;
+    for (uint32_t s = 0; s < n; s += segment) {
+        uint32_t m = n - s < segment ? n - s : segment;
+        if (or_stable_sort(keys + s, m, perm + s, NULL))
+            return 1;
+        for (uint32_t i = 0; i < m; ++i)
+            perm[s + i] += s;
+        if (n - s <= segment)
+            break;
+    }
+    return 0;
+}
+
 /* out[i] = in[perm[i]] for every field of the ray SoA, bit for bit. */
 void or_permute(const float *o_tmin, const float *d_tmax, const uint32_t *payload,
                 const uint32_t *perm, uint32_t n, float *o_out, float *d_out, uint32_t *p_out)

@@ -281,6 +281,130 @@ __global__ void __launch_bounds__(kSortBlock, 3) onesweep_kernel(PassArgs<K> a) 
     }
 }
 
+// ------------------------------------------------------------------ local (segment) sort
+
+// One block sorts one segment of SEG = 256 * ITEMS consecutive keys entirely in
+// shared memory: an LSD pass per 8-bit digit, each ranking the keys in
+// position order (warp, item, lane) with the same warp-vote peer masks as the
+// global passes, then scattering them back to shared memory.  The tail segment
+// is padded with all-ones keys placed after the real keys, so stability keeps
+// the padding last.  perm receives global indices.
+template <typename K, int ITEMS>
+__global__ void __launch_bounds__(kSortBlock) segment_sort_kernel(const K *__restrict__ keys_in,
+                                                                 K *__restrict__ keys_out,
+                                                                 uint32_t *__restrict__ perm_out, uint32_t n,
+                                                                 uint32_t bits) {
+    constexpr int RBITS = 8, RADIX = 256;
+    constexpr int SEG = kSortBlock * ITEMS;
+    constexpr int WSEG = 32 * ITEMS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    K *s_keys = reinterpret_cast<K *>(smem_raw);
+    uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + SEG);
+    uint32_t *s_wh = s_vals + SEG;                 // [warps][RADIX]
+    uint32_t *s_dstart = s_wh + kSortWarps * RADIX;  // [RADIX]
+    uint32_t *s_scan = s_dstart + RADIX;           // scan scratch
+
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t base = blockIdx.x * (uint32_t)SEG;
+    const uint32_t m = min((uint32_t)SEG, n - base);
+    const uint32_t lt = lanemask_lt();
+    K k[ITEMS];
+    uint32_t v[ITEMS], r[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t pos = warp * WSEG + j * 32 + lane;
+        k[j] = pos < m ? keys_in[base + pos] : ~(K)0;
+        v[j] = pos;
+    }
+    const uint32_t passes = (bits + RBITS - 1) / RBITS;
+    for (uint32_t p = 0; p < passes; ++p) {
+        const uint32_t shift = p * RBITS;
+        const uint32_t mask = (1u << min((uint32_t)RBITS, bits - shift)) - 1u;
+        for (uint32_t i = tid; i < kSortWarps * RADIX; i += kSortBlock) s_wh[i] = 0;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) r[j] = digit_peers<RBITS>(digit_of(k[j], shift, mask), 0xFFFFFFFFu);
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const uint32_t dg = digit_of(k[j], shift, mask);
+            const uint32_t peers = r[j];
+            const uint32_t cur = s_wh[warp * RADIX + dg];
+            __syncwarp();
+            if (lane == 31u - __clz(peers)) s_wh[warp * RADIX + dg] = cur + __popc(peers);
+            __syncwarp();
+            r[j] = cur + __popc(peers & lt);
+        }
+        __syncthreads();
+        uint32_t cnt = 0;
+        if (tid < RADIX) {
+            for (int w = 0; w < kSortWarps; ++w) {
+                const uint32_t c = s_wh[w * RADIX + tid];
+                s_wh[w * RADIX + tid] = cnt;
+                cnt += c;
+            }
+        }
+        const uint32_t start = scan_digits<RADIX>(cnt, s_scan);
+        if (tid < RADIX) s_dstart[tid] = start;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const uint32_t dg = digit_of(k[j], shift, mask);
+            const uint32_t pos = s_dstart[dg] + s_wh[warp * RADIX + dg] + r[j];
+            s_keys[pos] = k[j];
+            s_vals[pos] = v[j];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const uint32_t pos = warp * WSEG + j * 32 + lane;
+            k[j] = s_keys[pos];
+            v[j] = s_vals[pos];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t pos = warp * WSEG + j * 32 + lane;
+        if (pos < m) {
+            perm_out[base + pos] = base + v[j];
+            if (keys_out) keys_out[base + pos] = k[j];
+        }
+    }
+}
+
+template <typename K, int ITEMS>
+static size_t segment_smem() {
+    return (sizeof(K) + sizeof(uint32_t)) * kSortBlock * ITEMS + sizeof(uint32_t) * (kSortWarps * 256 + 256 + 16);
+}
+
+template <typename K, int ITEMS>
+static cudaError_t launch_segment_sort(const K *keys_in, K *keys_out, uint32_t *perm_out, uint32_t n, uint32_t bits,
+                                       cudaStream_t s) {
+    const size_t smem = segment_smem<K, ITEMS>();
+    static bool configured = false;
+    if (!configured) {
+        const cudaError_t e = cudaFuncSetAttribute(segment_sort_kernel<K, ITEMS>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const uint32_t seg = kSortBlock * ITEMS;
+    segment_sort_kernel<K, ITEMS><<<(n + seg - 1) / seg, kSortBlock, smem, s>>>(keys_in, keys_out, perm_out, n, bits);
+    return cudaGetLastError();
+}
+
+template <typename K>
+static cudaError_t dispatch_segment_sort(const K *ki, K *ko, uint32_t *perm, uint32_t n, uint32_t bits,
+                                         uint32_t segment, cudaStream_t s) {
+    switch (segment) {
+        case 256: return launch_segment_sort<K, 1>(ki, ko, perm, n, bits, s);
+        case 512: return launch_segment_sort<K, 2>(ki, ko, perm, n, bits, s);
+        case 1024: return launch_segment_sort<K, 4>(ki, ko, perm, n, bits, s);
+        case 2048: return launch_segment_sort<K, 8>(ki, ko, perm, n, bits, s);
+        default: return launch_segment_sort<K, 16>(ki, ko, perm, n, bits, s);
+    }
+}
+
 // ------------------------------------------------------------------ host side
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -434,6 +558,33 @@ extern "C" rr_status rr_sort(const void *keys_in, void *keys_out, uint32_t *perm
     return radix_bits == 8
                ? run_sort<unsigned long long, 8>(pl, ki, ko, perm_out, n, bits, ws, ds->err, ds->sm_count, s)
                : run_sort<unsigned long long, 4>(pl, ki, ko, perm_out, n, bits, ws, ds->err, ds->sm_count, s);
+}
+
+extern "C" rr_status rr_sort_segments(const void *keys_in, void *keys_out, uint32_t *perm_out, uint32_t n,
+                                      uint32_t bits, uint32_t segment, void *stream) {
+    if (bits < 1 || bits > 64) return fail(RR_ERR_INVALID_ARG, "rr_sort_segments: bits not in 1..64");
+    if (segment != 256 && segment != 512 && segment != 1024 && segment != 2048 && segment != 4096)
+        return fail(RR_ERR_INVALID_ARG, "rr_sort_segments: segment must be 256, 512, 1024, 2048 or 4096");
+    if (n >= (1u << 30)) return fail(RR_ERR_INVALID_ARG, "rr_sort_segments: n must be < 2^30");
+    if (n == 0) return RR_OK;
+    if (!keys_in || !perm_out) return fail(RR_ERR_INVALID_ARG, "rr_sort_segments: NULL buffer");
+    const size_t kb = bits > 32 ? 8 : 4, kbytes = kb * n;
+    if (!aligned(keys_in, kb) || (keys_out && !aligned(keys_out, kb)) || !aligned(perm_out, 4))
+        return fail(RR_ERR_INVALID_ARG, "rr_sort_segments: misaligned buffer");
+    if (overlaps(keys_in, kbytes, perm_out, 4ull * n) ||
+        (keys_out && (overlaps(keys_out, kbytes, keys_in, kbytes) || overlaps(keys_out, kbytes, perm_out, 4ull * n))))
+        return fail(RR_ERR_INVALID_ARG, "rr_sort_segments: buffers overlap");
+    rr_status st;
+    if (!device_state(&st)) return st;
+    cudaStream_t s = as_stream(stream);
+    const cudaError_t e =
+        kb == 4 ? dispatch_segment_sort(static_cast<const uint32_t *>(keys_in), static_cast<uint32_t *>(keys_out),
+                                        perm_out, n, bits, segment, s)
+                : dispatch_segment_sort(static_cast<const unsigned long long *>(keys_in),
+                                        static_cast<unsigned long long *>(keys_out), perm_out, n, bits, segment, s);
+    if (e != cudaSuccess) return fail_cuda(e, "rr_sort_segments");
+    note_launches(1);
+    return RR_OK;
 }
 
 // ------------------------------------------------------------------ sort without allocation

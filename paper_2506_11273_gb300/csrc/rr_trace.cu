@@ -9,6 +9,11 @@
 // direction octant); the leaves a node's children hit are tested at once.
 // Triangles are intersected with Moller-Trumbore in fp32 and the winning
 // distance is refined in compensated fp32.
+//
+// Two variants serve the reordering study: indirect access (the queue hands
+// out positions of an index buffer, so sorted rays are traced without being
+// gathered first, Section 5) and any-hit traversal for shadow rays (the first
+// triangle found inside the interval ends the ray, Section 4).
 #include <chrono>
 #include <cmath>
 
@@ -27,6 +32,7 @@ struct TraceArgs {
     const float4 *o_tmin;
     const float4 *d_tmax;
     float4 *hits;
+    const uint32_t *order;  // NULL: position k traces ray k; else ray order[k]
     uint32_t n;
     uint32_t n_nodes;
     uint32_t *queue;  // [0] next ray, [1] finished blocks
@@ -219,7 +225,9 @@ __device__ __forceinline__ bool ray_visit_node(RayState &r, uint2 *stack, const 
     return true;
 }
 
-// Tests every triangle of the pending group.
+// Tests every triangle of the pending group.  ANY: the first hit ends the ray
+// (the pending group, the current node group and the stack are dropped).
+template <bool ANY>
 __device__ __forceinline__ void ray_test_triangles(RayState &r, const TraceArgs &a) {
     const float tmin = r.o.w;
     while (r.t_hits != 0u) {
@@ -250,6 +258,12 @@ __device__ __forceinline__ void ray_test_triangles(RayState &r, const TraceArgs 
             r.bv = v;
             r.best_tri = __float_as_uint(v0.w);
             r.best_k = k;
+            if (ANY) {
+                r.t_hits = 0u;
+                r.g_hits = 0u;
+                r.sp = 0;
+                return;
+            }
         }
     }
 }
@@ -281,7 +295,7 @@ __device__ __forceinline__ void accumulate_hit(const TraceArgs &a, const QuantFr
     atomicAdd(a.table + 2 * (size_t)cell + 1, 1ull);
 }
 
-template <bool ACCUM>
+template <bool ACCUM, bool ANY>
 __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceArgs a) {
     const uint32_t lane = threadIdx.x & 31u;
     uint2 stack[kTraceStack];
@@ -298,8 +312,13 @@ __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceArgs a) {
         if (base >= a.n) break;
 #pragma unroll 1
         for (uint32_t k = 0; k < kQueueBatch; k += 32) {
-            const uint32_t i = base + k + lane;
-            if (i >= a.n) break;
+            const uint32_t pos = base + k + lane;
+            if (pos >= a.n) break;
+            const uint32_t i = a.order ? __ldg(a.order + pos) : pos;
+            if (i >= a.n) {  // not a permutation of [0, n): record and skip
+                atomicOr(a.err, RR_DEVERR_BAD_INDEX);
+                continue;
+            }
             RayState r;
             const float4 o = __ldg(a.o_tmin + i), d = __ldg(a.d_tmax + i);
             ray_begin(r, a, o, d);
@@ -309,7 +328,7 @@ __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceArgs a) {
                     r.best_tri = kMiss;
                     break;
                 }
-                ray_test_triangles(r, a);
+                ray_test_triangles<ANY>(r, a);
                 if (r.g_hits == 0u) {
                     if (r.sp == 0) break;
                     const uint2 e = stack[--r.sp];
@@ -414,26 +433,36 @@ extern "C" rr_status rr_bvh_get_info(const rr_bvh *b, rr_bvh_info *info) {
 
 namespace {
 
-rr_status launch_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax, uint32_t n, float *hits_out,
-                       rr_length_table *table, void *stream, const char *what) {
+template <bool ACC, bool ANY>
+int trace_blocks_per_sm() {
+    static int bps = 0;
+    if (bps == 0) {
+        int v = 0;
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, trace_kernel<ACC, ANY>, kTraceBlock, 0);
+        bps = (e != cudaSuccess || v < 1) ? 1 : v;
+    }
+    return bps;
+}
+
+rr_status launch_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax, const uint32_t *order, uint32_t n,
+                       float *hits_out, uint32_t flags, rr_length_table *table, void *stream, const char *what) {
     if (!b) return fail(RR_ERR_INVALID_ARG, std::string(what) + ": NULL bvh");
+    if (flags & ~(uint32_t)RR_TRACE_ANY_HIT) return fail(RR_ERR_INVALID_ARG, std::string(what) + ": unknown flags");
+    const bool any = (flags & RR_TRACE_ANY_HIT) != 0;
+    if (any && table)
+        return fail(RR_ERR_INVALID_ARG, std::string(what) + ": any-hit distances are not ray lengths for the table");
     if (n == 0) return RR_OK;
     if (!o_tmin || !d_tmax || !hits_out) return fail(RR_ERR_INVALID_ARG, std::string(what) + ": NULL buffer");
-    if (!aligned16(o_tmin) || !aligned16(d_tmax) || !aligned16(hits_out))
-        return fail(RR_ERR_INVALID_ARG, std::string(what) + ": buffers not 16-byte aligned");
-    if (overlaps(hits_out, 16ull * n, o_tmin, 16ull * n) || overlaps(hits_out, 16ull * n, d_tmax, 16ull * n))
-        return fail(RR_ERR_INVALID_ARG, std::string(what) + ": hits overlap the rays");
+    if (!aligned16(o_tmin) || !aligned16(d_tmax) || !aligned16(hits_out) || !aligned(order, 4))
+        return fail(RR_ERR_INVALID_ARG, std::string(what) + ": misaligned buffer");
+    if (overlaps(hits_out, 16ull * n, o_tmin, 16ull * n) || overlaps(hits_out, 16ull * n, d_tmax, 16ull * n) ||
+        (order && overlaps(hits_out, 16ull * n, order, 4ull * n)))
+        return fail(RR_ERR_INVALID_ARG, std::string(what) + ": hits overlap an input");
     rr_status st;
     DeviceState *ds = device_state(&st);
     if (!ds) return st;
-    static int blocks_per_sm[2] = {0, 0};
-    const int acc = table ? 1 : 0;
-    if (blocks_per_sm[acc] == 0) {
-        int bps = 0;
-        cudaError_t e = acc ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, trace_kernel<true>, kTraceBlock, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, trace_kernel<false>, kTraceBlock, 0);
-        blocks_per_sm[acc] = (e != cudaSuccess || bps < 1) ? 1 : bps;
-    }
+    const int bps = table ? trace_blocks_per_sm<true, false>()
+                          : (any ? trace_blocks_per_sm<false, true>() : trace_blocks_per_sm<false, false>());
     const uint32_t slot = ds->next_counter.fetch_add(1) % (kCounterPool / 2);
     TraceArgs a;
     a.nodes = reinterpret_cast<const float4 *>(b->nodes);
@@ -442,6 +471,7 @@ rr_status launch_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax
     a.o_tmin = reinterpret_cast<const float4 *>(o_tmin);
     a.d_tmax = reinterpret_cast<const float4 *>(d_tmax);
     a.hits = reinterpret_cast<float4 *>(hits_out);
+    a.order = order;
     a.n = n;
     a.n_nodes = b->n_nodes;
     a.queue = ds->counters + 2 * slot;
@@ -452,12 +482,15 @@ rr_status launch_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax
         a.thi[c] = table ? table->box.hi[c] : 0.0f;
     }
     const uint32_t want = (n + kQueueBatch - 1) / kQueueBatch;  // warps that can get work
-    uint32_t grid = (uint32_t)ds->sm_count * (uint32_t)blocks_per_sm[acc];
+    uint32_t grid = (uint32_t)ds->sm_count * (uint32_t)bps;
     grid = std::max(1u, std::min(grid, (want + kTraceBlock / 32 - 1) / (kTraceBlock / 32)));
+    cudaStream_t s = as_stream(stream);
     if (table)
-        trace_kernel<true><<<grid, kTraceBlock, 0, as_stream(stream)>>>(a);
+        trace_kernel<true, false><<<grid, kTraceBlock, 0, s>>>(a);
+    else if (any)
+        trace_kernel<false, true><<<grid, kTraceBlock, 0, s>>>(a);
     else
-        trace_kernel<false><<<grid, kTraceBlock, 0, as_stream(stream)>>>(a);
+        trace_kernel<false, false><<<grid, kTraceBlock, 0, s>>>(a);
     note_launches(1);
     return check_launch(what);
 }
@@ -466,11 +499,16 @@ rr_status launch_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax
 
 extern "C" rr_status rr_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax, uint32_t n, float *hits_out,
                               void *stream) {
-    return launch_trace(b, o_tmin, d_tmax, n, hits_out, nullptr, stream, "rr_trace");
+    return launch_trace(b, o_tmin, d_tmax, nullptr, n, hits_out, 0u, nullptr, stream, "rr_trace");
 }
 
 extern "C" rr_status rr_trace_accumulate(const rr_bvh *b, const float *o_tmin, const float *d_tmax, uint32_t n,
                                          float *hits_out, rr_length_table *table, void *stream) {
     if (!table) return fail(RR_ERR_INVALID_ARG, "rr_trace_accumulate: NULL table");
-    return launch_trace(b, o_tmin, d_tmax, n, hits_out, table, stream, "rr_trace_accumulate");
+    return launch_trace(b, o_tmin, d_tmax, nullptr, n, hits_out, 0u, table, stream, "rr_trace_accumulate");
+}
+
+extern "C" rr_status rr_trace_ex(const rr_bvh *b, const float *o_tmin, const float *d_tmax, const uint32_t *order,
+                                 uint32_t n, float *hits_out, uint32_t flags, rr_length_table *table, void *stream) {
+    return launch_trace(b, o_tmin, d_tmax, order, n, hits_out, flags, table, stream, "rr_trace_ex");
 }

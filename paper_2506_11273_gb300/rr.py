@@ -30,6 +30,8 @@ RR_KEY_ORIGIN, RR_KEY_REIS, RR_KEY_COSTA, RR_KEY_OCTAHEDRON = 3, 4, 5, 6
 RR_T_FIXED, RR_T_ADAPTIVE, RR_T_GIVEN = 0, 1, 2
 RR_DEVERR_LOOKBACK_TIMEOUT = 0x1
 RR_DEVERR_TRACE_STACK = 0x2
+RR_DEVERR_BAD_INDEX = 0x4
+RR_TRACE_ANY_HIT = 0x1
 MISS = 0xFFFFFFFF
 TABLE_CELLS = 1 << 20
 
@@ -45,7 +47,7 @@ EXPORTS = [
     "rr_length_table_write", "rr_length_table_destroy", "rr_pipeline_create",
     "rr_pipeline_destroy", "rr_pipeline_run", "rr_pipeline_run_host", "rr_device_error",
     "rr_status_string", "rr_last_error_message", "rr_kernel_launch_count", "rr_sort_noalloc",
-    "rr_coherence_capsule",
+    "rr_coherence_capsule", "rr_trace_ex", "rr_sort_segments",
 ]
 
 
@@ -98,6 +100,8 @@ def lib():
             L.rr_pipeline_destroy.argtypes = [vp]
             L.rr_pipeline_run.argtypes = [vp, vp, vp, vp, u32, vp, vp, vp]
             L.rr_pipeline_run_host.argtypes = [vp, vp, vp, vp, u32, vp, vp, vp]
+            L.rr_sort_segments.argtypes = [vp, vp, vp, u32, u32, u32, vp]
+            L.rr_trace_ex.argtypes = [vp, vp, vp, vp, u32, vp, u32, vp, vp]
             L.rr_coherence_capsule.argtypes = [vp, vp, vp, u32, u32, C.c_float, vp, vp]
             L.rr_device_error.argtypes = [C.POINTER(C.c_uint32)]
             L.rr_status_string.argtypes = [i32]
@@ -183,6 +187,12 @@ def rr_sort(keys_in, keys_out, perm_out, n: int, bits: int, radix_bits: int, wor
                          _ptr(workspace), nbytes, _stream(stream)), "rr_sort")
 
 
+def rr_sort_segments(keys_in, keys_out, perm_out, n: int, bits: int, segment: int, stream=None):
+    """Stable sort inside each run of `segment` consecutive keys (local sort)."""
+    _check(lib().rr_sort_segments(_ptr(keys_in), _ptr(keys_out), _ptr(perm_out), n, bits, segment,
+                                  _stream(stream)), "rr_sort_segments")
+
+
 def rr_sort_noalloc(keys_in, keys_out, perm_out, n: int, bits: int, radix_bits: int, stream=None):
     """rr_sort without a workspace argument, for callers that cannot allocate device
     memory (n <= RR_SORT_NOALLOC_MAX_N).  Errors come back as the status only."""
@@ -257,6 +267,15 @@ def rr_trace_accumulate(bvh: BVH, o_tmin, d_tmax, hits_out, table: "LengthTable"
     n = o_tmin.shape[0] if n is None else n
     _check(lib().rr_trace_accumulate(bvh.handle, _ptr(o_tmin), _ptr(d_tmax), n, _ptr(hits_out),
                                      table.handle, _stream(stream)), "rr_trace_accumulate")
+
+
+def rr_trace_ex(bvh: BVH, o_tmin, d_tmax, hits_out, order=None, flags: int = 0, table: "LengthTable" = None,
+                n: int | None = None, stream=None):
+    """Trace with an optional index buffer (indirect access) and any-hit flag."""
+    n = o_tmin.shape[0] if n is None else n
+    _check(lib().rr_trace_ex(bvh.handle, _ptr(o_tmin), _ptr(d_tmax), _ptr(order) if order is not None else None,
+                             n, _ptr(hits_out), flags, table.handle if table is not None else None,
+                             _stream(stream)), "rr_trace_ex")
 
 
 # ---------------------------------------------------------------- ray-length table

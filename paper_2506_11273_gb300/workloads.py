@@ -379,3 +379,27 @@ def random_rays_in_box(n: int, lo, hi, seed: int, tmin: float = 0.0, tmax: float
     d = _normalize(rng.normal(size=(n, 3)))
     return make_rays(o.astype(np.float32), d.astype(np.float32), np.float32(tmin),
                      np.float32(tmax), np.arange(n, dtype=np.uint32))
+
+
+def shadow_rays(tris: np.ndarray, n: int, seed: int, light_center=None, light_frac: float = 0.05,
+                tmin: float = 1e-4) -> Rays:
+    """Next-event-estimation shadow rays: origins uniform by area on the soup,
+    each aimed at a uniform point of a square area light whose side is
+    ``light_frac`` of the largest scene extent (the evaluation setup of
+    Section 4), placed above the scene's centre unless ``light_center`` is given.
+    d = light point - origin (not normalised), so the segment is t in
+    (tmin, 1 - 1e-4); in random order."""
+    rng = rng_for(seed * 13 + 5)
+    lo, hi = scene_aabb(tris)
+    lo = lo.astype(np.float64)
+    hi = hi.astype(np.float64)
+    E = float(np.max(hi - lo))
+    c = np.array([(lo[0] + hi[0]) / 2, hi[1] + 0.05 * E, (lo[2] + hi[2]) / 2]) if light_center is None \
+        else np.asarray(light_center, np.float64)
+    pts, _, _ = surface_points(tris, n, rng)
+    side = light_frac * E
+    lp = c[None, :] + np.stack([(rng.random(n) - 0.5) * side, np.zeros(n), (rng.random(n) - 0.5) * side], axis=1)
+    d = lp - pts
+    perm = rng.permutation(n)
+    return make_rays(pts[perm].astype(np.float32), d[perm].astype(np.float32), np.float32(tmin),
+                     np.float32(1.0 - 1e-4), perm.astype(np.uint32))

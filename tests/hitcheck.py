@@ -83,3 +83,50 @@ def compare(tris, o_tmin, d_tmax, gpu_hits, or_hits, or_info, max_ambiguous=None
     limit = max(1, AMBIGUOUS_FRACTION * n) if max_ambiguous is None else max_ambiguous
     assert len(ambiguous) <= limit, res
     return res
+
+
+def compare_any_hit(tris, o_tmin, d_tmax, gpu_hits, or_hits, or_info, max_ambiguous=None):
+    """Any-hit rule: a ray is occluded exactly when the oracle finds a closest
+    hit; the triangle the GPU reports must itself be met inside (tmin, tmax) at
+    the reported t (1e-5 relative).  Edge, grazing and interval-end rays are
+    classified as in ``compare``."""
+    tris = np.ascontiguousarray(tris, np.float32).reshape(-1, 9)
+    n = o_tmin.shape[0]
+    g_tri = np.ascontiguousarray(gpu_hits[:, 3]).view(np.uint32)
+    o_tri = np.ascontiguousarray(or_hits[:, 3]).view(np.uint32)
+    g_occ = g_tri != oracle.MISS
+    o_occ = o_tri != oracle.MISS
+    ambiguous, definite = [], []
+    for i in range(n):
+        if not g_occ[i] and not o_occ[i]:
+            continue
+        o = o_tmin[i, :3].astype(np.float64)
+        d = d_tmax[i, :3].astype(np.float64)
+        tmin, tmax = float(o_tmin[i, 3]), float(d_tmax[i, 3])
+        amb = False
+        if g_occ[i]:
+            gt = int(g_tri[i])
+            ok, tp, mg = _plane_hit(o, d, tris, gt)
+            inside = ok and mg >= 0.0 and tmin < tp < tmax and abs(gpu_hits[i, 0] - tp) <= T_REL * abs(tp)
+            amb_g = ok and (abs(mg) < EDGE_MARGIN or _cos(d, tris, gt) < GRAZING_COS or
+                            _near_interval_end(tp, tmin, tmax))
+            if not inside:
+                (ambiguous if amb_g else definite).append(i)
+                continue
+            if o_occ[i]:
+                continue
+            amb = amb_g
+        else:
+            ot = int(o_tri[i])
+            amb = or_info[i, 1] < EDGE_MARGIN or _cos(d, tris, ot) < GRAZING_COS or \
+                _near_interval_end(or_info[i, 0], tmin, tmax)
+        (ambiguous if amb else definite).append(i)
+    res = dict(n=n, occluded=int(o_occ.sum()), ambiguous=len(ambiguous), definite=len(definite))
+    if definite:
+        i = definite[0]
+        raise AssertionError("any-hit mismatch on %d of %d rays, e.g. ray %d: gpu (t=%r, tri=%d) oracle "
+                             "(t=%r, tri=%d)" % (len(definite), n, i, gpu_hits[i, 0], g_tri[i], or_info[i, 0],
+                                                 o_tri[i]))
+    limit = max(1, AMBIGUOUS_FRACTION * n) if max_ambiguous is None else max_ambiguous
+    assert len(ambiguous) <= limit, res
+    return res

@@ -62,6 +62,25 @@ def test_sort_full_64bit_range():
     assert perm.tolist() == [1, 5, 3, 2, 0, 4]
 
 
+@pytest.mark.parametrize("n,segment", [(0, 4), (1, 1), (10, 1), (10, 3), (1000, 64), (1000, 1000),
+                                       (1000, 4096), (4097, 1024)])
+def test_segment_sort_invariants(n, segment):
+    """Each segment holds a stable sort of its own keys; segment >= n is the
+    global sort and segment 1 the identity."""
+    rng = np.random.default_rng(n + segment)
+    keys = rng.integers(0, 9, size=n).astype(np.uint64) << np.uint64(30)
+    perm = oracle.segment_sort(keys, segment)
+    for s in range(0, n, segment):
+        seg = perm[s:s + segment]
+        assert np.array_equal(np.sort(seg), np.arange(s, min(n, s + segment), dtype=np.uint32))
+        ref = sorted(range(s, min(n, s + segment)), key=lambda i: int(keys[i]))
+        assert seg.tolist() == ref
+    if segment >= n:
+        assert np.array_equal(perm, oracle.stable_sort(keys)[0])
+    if segment == 1:
+        assert np.array_equal(perm, np.arange(n, dtype=np.uint32))
+
+
 def test_permute_is_bitwise_gather():
     rng = np.random.default_rng(2)
     n = 777
