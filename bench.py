@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--bounce", type=int, default=3)
     ap.add_argument("--small", action="store_true", help="tiny scene and wavefront (for profiling runs)")
     ap.add_argument("--no-extra", action="store_true", help="skip the per-bounce and e2e sweeps")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-execution measurement")
     return ap.parse_args()
 
 
@@ -417,11 +418,106 @@ def run_ours(args):
         "setup_s": round(setup_s, 1),
     }
     out.update(extra)
+    if not args.no_batched:
+        out["batched"] = bench_batched(args, dev, flush)
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline(tris, lo, hi, sample=20000 if args.small else 100000)
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- batched
+
+# 4 resident scenes of ~50k, 250k, 1M and 2M triangles built like the path-tracer
+# scene: (cells_x, cells_z, boxes) with 90% heightfield and 10% box triangles
+BATCH_SCENES = [(112, 200, 417), (237, 475, 2083), (474, 949, 8333), (671, 1341, 16667)]
+BATCH_WAVEFRONTS = 32
+
+
+def bench_batched(args, dev, flush):
+    """32 wavefronts of log-uniform 10k-2M rays over 4 resident scenes: the
+    autotuned batch as one CUDA-graph launch versus the per-wavefront launch
+    loop (same configuration), and the unsorted per-wavefront trace."""
+    import torch
+
+    from paper_2506_11273_gb300 import rr
+    from paper_2506_11273_gb300 import workloads as W
+
+    rng = np.random.default_rng(4)
+    scale = 0.05 if args.small else 1.0
+    sizes = np.exp(rng.uniform(np.log(1e4 * scale), np.log(2e6 * scale), BATCH_WAVEFRONTS)).astype(np.int64)
+    which = rng.integers(0, len(BATCH_SCENES), BATCH_WAVEFRONTS)
+    scenes, bvhs, boxes = [], [], []
+    for k, (cx, cz, nb) in enumerate(BATCH_SCENES):
+        if args.small:
+            cx, cz, nb = max(8, cx // 8), max(16, cz // 8), max(10, nb // 64)
+        t = W.scene_terrain(seed=40 + k, cells_x=cx, cells_z=cz, n_boxes=nb)
+        scenes.append(t)
+        bvhs.append(rr.BVH(t))
+        boxes.append(W.scene_aabb(t))
+    o_parts, d_parts, fronts = [], [], []
+    for k in range(BATCH_WAVEFRONTS):
+        s = int(which[k])
+        r = W.surface_rays(scenes[s], int(sizes[k]), seed=500 + k)
+        o_parts.append(r.o_tmin)
+        d_parts.append(r.d_tmax)
+        fronts.append((bvhs[s], None, boxes[s][0], boxes[s][1], int(sizes[k])))
+    o = torch.from_numpy(np.concatenate(o_parts)).to(dev)
+    d = torch.from_numpy(np.concatenate(d_parts)).to(dev)
+    del o_parts, d_parts
+    batch = rr.Batch(fronts, rr.RR_KEY_TWO_POINT, rr.RR_T_FIXED)
+    n = batch.n
+    hits = torch.empty(n, 4, device=dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    t0 = time.time()
+    cfg, tuned_ms = batch.tune(o, d, hits)
+    tune_s = time.time() - t0
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, K):
+        for _ in range(3):
+            flush.zero_()
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(K):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / K
+
+    K = 5
+    ms_graph = timed(lambda: batch.run(o, d, hits, cfg, perm), K)
+    l0 = rr.rr_kernel_launch_count()
+    ms_loop = timed(lambda: batch.run_loop(o, d, hits, cfg, perm), K)
+    loop_launches = (rr.rr_kernel_launch_count() - l0) // (K + 3)
+    offs = batch.offsets
+
+    def unsorted():
+        for k in range(BATCH_WAVEFRONTS):
+            a, b_ = offs[k], offs[k + 1]
+            rr.rr_trace(fronts[k][0], o[a:b_], d[a:b_], hits[a:b_])
+    ms_uns = timed(unsorted, K)
+    if rr.rr_device_error() != 0:
+        raise RuntimeError("device error flag set during the batched measurement")
+    out = {"workload": "%d wavefronts of log-uniform %d-%d rays over %d scenes of %s triangles; Two Point "
+                       "key (fixed estimate)" % (BATCH_WAVEFRONTS, int(1e4 * scale), int(2e6 * scale),
+                                                 len(scenes), "/".join(str(t.shape[0]) for t in scenes)),
+           "rays": int(n), "autotuned": {"key_bits": cfg.key_bits, "radix_bits": cfg.radix_bits,
+                                          "trace_block": cfg.trace_block, "tuned_ms": round(tuned_ms, 3),
+                                          "tune_s": round(tune_s, 2)},
+           "graph_ms": round(ms_graph, 3), "graph_mrays": round(n / (ms_graph * 1e-3) / 1e6, 1),
+           "graph_kernels": 3 + -(-(cfg.key_bits + batch.info()["seg_bits"]) // cfg.radix_bits),
+           "loop_ms": round(ms_loop, 3), "loop_mrays": round(n / (ms_loop * 1e-3) / 1e6, 1),
+           "loop_launches": int(loop_launches),
+           "unsorted_loop_ms": round(ms_uns, 3), "unsorted_loop_mrays": round(n / (ms_uns * 1e-3) / 1e6, 1)}
+    batch.close()
+    return out
 
 
 # ----------------------------------------------------------------------------- oracle

@@ -348,6 +348,89 @@ rr_status rr_pipeline_run_host(rr_pipeline *p, const float *o_tmin_host, const f
 rr_status rr_coherence_capsule(const float *o_tmin, const float *d_tmax, const float *hits, uint32_t n,
                                uint32_t subset, float E, float *areas_out, void *stream);
 
+/* ---------------------------------------------------------------- batched execution */
+
+/*
+ * A batch is many wavefronts, each traced against one of several resident
+ * scenes, handled by one chain of launches: keys of every ray (each in its own
+ * wavefront's box and table), one stable radix sort whose keys carry the
+ * wavefront number above the key's bits (so every wavefront is sorted on its
+ * own and stays in its range: the local sort of Section 3.2 with
+ * wavefront-sized segments), and one trace of all rays through the
+ * permutation (indirect access, Section 5), hits in input order.  The chain
+ * is captured once per configuration and buffer set into a CUDA graph and
+ * replayed (rr_batch_run); rr_batch_run_loop issues the same work wavefront
+ * by wavefront through the single-wavefront calls, with the same results.
+ *
+ * The rays of all wavefronts lie in one pair of buffers (o_tmin, d_tmax,
+ * float4 each); wavefront k holds rays [offset, offset + count), contiguous
+ * and in order.
+ */
+typedef struct {
+    const rr_bvh *bvh;        /* the scene this wavefront is traced against */
+    rr_length_table *table;   /* Two Point ADAPTIVE: the scene's table (read by the key,
+                                 updated by the trace); otherwise ignored */
+    float aabb_lo[3];         /* the quantisation box of the wavefront's keys */
+    float aabb_hi[3];
+    uint32_t offset;          /* first ray of the wavefront in the batch buffers */
+    uint32_t count;           /* rays of the wavefront (0 allowed) */
+} rr_wavefront;
+
+typedef struct {
+    uint32_t key_bits;     /* bits of each wavefront's own key; key_bits + wavefront bits <= 64 */
+    uint32_t radix_bits;   /* 4 or 8 */
+    uint32_t trace_block;  /* threads per trace block: 128, 256 or 512 */
+} rr_batch_config;
+
+typedef struct rr_batch rr_batch;
+
+/*
+ * rr_batch_create - validates 1..1024 wavefronts (the array is copied; BVHs and
+ * tables must outlive the batch) and allocates the batch's device memory
+ * (keys, permutation, sort workspace, descriptors).  layout/t_source/ratio as
+ * in rr_key_params; RR_T_GIVEN is not batched (RR_ERR_UNSUPPORTED).
+ * Synchronising.
+ */
+rr_status rr_batch_create(const rr_wavefront *fronts, uint32_t n_fronts, rr_key_layout layout,
+                          rr_t_source t_source, float ratio, rr_batch **out);
+rr_status rr_batch_destroy(rr_batch *batch);
+
+/* Rays in the batch, wavefront-number bits, graphs captured so far (each may be NULL). */
+rr_status rr_batch_info(const rr_batch *batch, uint32_t *n_rays, uint32_t *seg_bits, uint32_t *n_graphs);
+
+/*
+ * rr_batch_run - the whole batch as one CUDA graph launch on `stream`.  The
+ * graph for (cfg, o_tmin, d_tmax, hits_out, perm_out) is captured on first use
+ * and kept with the batch.  hits_out (device, float4 per ray) in input order;
+ * perm_out (device, uint32 per ray, or NULL): the batch permutation, whose
+ * range of wavefront k is the stable sort of that wavefront's keys (global
+ * indices).  Runs of one batch must not overlap in time (they share the
+ * batch's scratch); use one stream per batch.
+ */
+rr_status rr_batch_run(rr_batch *batch, const float *o_tmin, const float *d_tmax, float *hits_out,
+                       uint32_t *perm_out, const rr_batch_config *cfg, void *stream);
+
+/*
+ * rr_batch_run_loop - the same work without a graph, launched wavefront by
+ * wavefront through rr_compute_keys, rr_sort and rr_trace_ex (all keys first,
+ * so the tables are read as rr_batch_run reads them).  Same hits and tables as
+ * rr_batch_run; perm_out holds indices local to each wavefront (the batch
+ * permutation minus the wavefront's offset).
+ */
+rr_status rr_batch_run_loop(rr_batch *batch, const float *o_tmin, const float *d_tmax, float *hits_out,
+                            uint32_t *perm_out, const rr_batch_config *cfg, void *stream);
+
+/*
+ * rr_batch_tune - autotuner: times rr_batch_run on these buffers for key bits
+ * {12, 16, 20, 24, 32, 48, 64} (capped by the wavefront bits) x radix width {4, 8}
+ * at 256-thread trace blocks, then trace blocks of 128 and 512 for the winner,
+ * and returns the fastest configuration (mean of 3 timed runs after one
+ * warm-up) and its time.  Length tables are saved before and restored after,
+ * so tuning leaves them as it found them.  Synchronising.
+ */
+rr_status rr_batch_tune(rr_batch *batch, const float *o_tmin, const float *d_tmax, float *hits_out,
+                        rr_batch_config *best, float *best_ms, void *stream);
+
 /* ---------------------------------------------------------------- diagnostics */
 
 /* Reads and clears the current device's error word (RR_DEVERR_* flags); synchronising. */

@@ -1,0 +1,41 @@
+// Internal interface between the batch runtime and the kernels it enqueues.
+#pragma once
+
+#include "rr_common.cuh"
+#include "rr_keymath.cuh"
+
+namespace rr {
+
+constexpr uint32_t kMaxBatchSegments = 1024;
+
+// Device descriptor of one wavefront (segment) of a batch: its scene's BVH,
+// the quantisation frame of its box, and its length table (or null).
+struct BatchScene {
+    const float4 *nodes;
+    const float4 *tris;
+    const float4 *planes;
+    uint32_t n_nodes;
+    unsigned long long *table;  // cells {sum, count}; null: no adaptive estimate, no update
+    QuantFrame frame;           // make_frame of the wavefront's box (computed on the device)
+    float invE;                 // 1 / frame.E
+};
+
+// Fills frame and invE of segs[k] from boxes[k] (6 floats lo, hi) for k < n.
+cudaError_t launch_batch_frames(BatchScene *segs, const float *boxes, uint32_t n, cudaStream_t s);
+
+// Keys of every ray of a batch: segment s in the bits above key_bits, the
+// wavefront's own key (layout, estimate) below.  keys: u32 when
+// key_bits + seg_bits <= 32, else u64.
+rr_status launch_keys_batch(const BatchScene *segs, const uint32_t *seg_offsets, uint32_t n_segs,
+                            rr_key_layout layout, rr_t_source tsrc, float ratio, uint32_t key_bits,
+                            uint32_t seg_bits, const float *o_tmin, const float *d_tmax, uint32_t n, void *keys,
+                            cudaStream_t s);
+
+// Closest-hit trace of a batch through `order`, hits in input order; the
+// length tables of the segments are updated when `accumulate`.  queue: two
+// device words at zero, owned by the caller.
+rr_status launch_trace_batch(const BatchScene *segs, const uint32_t *seg_offsets, uint32_t n_segs, const float *o_tmin,
+                             const float *d_tmax, const uint32_t *order, uint32_t n, float *hits_out,
+                             bool accumulate, uint32_t block, uint32_t *queue, cudaStream_t s);
+
+}  // namespace rr

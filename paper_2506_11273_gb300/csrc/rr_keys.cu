@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "rr_batch.cuh"
 #include "rr_common.cuh"
 #include "rr_keymath.cuh"
 
@@ -20,14 +21,12 @@ struct KeyArgs {
     void *keys;
 };
 
-// One ray per thread: two 16-byte loads, quantisation, interleave, one store.
-template <int LAYOUT, int TSRC, typename KeyT>
-__global__ void __launch_bounds__(256) key_kernel(KeyArgs a) {
-    const QuantFrame f = block_frame(a.lo, a.hi);
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    float4 o = __ldg(a.o_tmin + i);
-    float4 d = __ldg(a.d_tmax + i);
+// The key of one ray (Section 3.1): the first `bits` bits of its layout's
+// string, in the frame of the quantisation box.  t_given: the GIVEN estimate;
+// table: the ADAPTIVE cells.
+template <int LAYOUT, int TSRC>
+__device__ __forceinline__ uint64_t ray_key(const QuantFrame &f, float4 o, float4 d, uint32_t bits, float ratio,
+                                            float t_given, const ulonglong2 *table) {
     uint32_t qo[3], qd[3];
     float dh[3];
     quantise_ray(f, o, d, qo, qd, dh);
@@ -35,12 +34,12 @@ __global__ void __launch_bounds__(256) key_kernel(KeyArgs a) {
     if (LAYOUT == RR_KEY_TWO_POINT) {
         float t;
         if (TSRC == RR_T_FIXED) {
-            t = __fmul_rn(a.ratio, f.E);
+            t = __fmul_rn(ratio, f.E);
         } else if (TSRC == RR_T_GIVEN) {
-            t = __ldg(a.t_given + i);
+            t = t_given;
         } else {
             // mean length of the ray's cell, in units of E / 2^24
-            ulonglong2 cell = __ldg(a.table + table_cell(qo, qd));
+            ulonglong2 cell = __ldg(table + table_cell(qo, qd));
             if (cell.y == 0ull) {
                 t = __fmul_rn(0.25f, f.E);
             } else {
@@ -65,21 +64,64 @@ __global__ void __launch_bounds__(256) key_kernel(KeyArgs a) {
     } else if (LAYOUT == RR_KEY_REIS || LAYOUT == RR_KEY_COSTA) {
         // two prefixes of their own Morton strings; the 32-bit split of Figure 2
         // (22 + 10 and 8 + 24) scaled to `bits`
-        const uint32_t db = LAYOUT == RR_KEY_REIS ? (a.bits * 10u) / 32u : (a.bits * 8u) / 32u;
-        const uint32_t ob = a.bits - db;
+        const uint32_t db = LAYOUT == RR_KEY_REIS ? (bits * 10u) / 32u : (bits * 8u) / 32u;
+        const uint32_t ob = bits - db;
         const uint64_t ko = prefix64(morton3_64(qo[0], qo[1], qo[2]), ob);
         const uint64_t kd = prefix64(morton3_64(qd[0], qd[1], qd[2]), db);
-        const uint64_t key = LAYOUT == RR_KEY_REIS ? (db ? (ko << db) | kd : ko) : (ob ? (kd << ob) | ko : kd);
-        static_cast<KeyT *>(a.keys)[i] = (KeyT)key;
-        return;
+        return LAYOUT == RR_KEY_REIS ? (db ? (ko << db) | kd : ko) : (ob ? (kd << ob) | ko : kd);
     } else {
         float u, v;
         octahedral(d.x, d.y, d.z, u, v);
         const uint32_t c[5] = {qo[0], qo[1], qo[2], quantise_unit(u) >> 4, quantise_unit(v) >> 4};
         key64 = interleave_octa_64(c);
     }
-    uint64_t key = key64 >> (64 - a.bits);
-    static_cast<KeyT *>(a.keys)[i] = (KeyT)key;
+    return key64 >> (64 - bits);
+}
+
+// One ray per thread: two 16-byte loads, quantisation, interleave, one store.
+template <int LAYOUT, int TSRC, typename KeyT>
+__global__ void __launch_bounds__(256) key_kernel(KeyArgs a) {
+    const QuantFrame f = block_frame(a.lo, a.hi);
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const float4 o = __ldg(a.o_tmin + i), d = __ldg(a.d_tmax + i);
+    const float tg = TSRC == RR_T_GIVEN ? __ldg(a.t_given + i) : 0.0f;
+    static_cast<KeyT *>(a.keys)[i] = (KeyT)ray_key<LAYOUT, TSRC>(f, o, d, a.bits, a.ratio, tg, a.table);
+}
+
+// Batches: the key of ray i in the frame (and table) of its segment, with the
+// segment number above the key's bits.
+template <int LAYOUT, int TSRC, typename KeyT>
+__global__ void __launch_bounds__(256) key_batch_kernel(const BatchScene *__restrict__ segs,
+                                                        const uint32_t *__restrict__ seg_offsets, uint32_t n_segs,
+                                                        const float4 *__restrict__ o_tmin,
+                                                        const float4 *__restrict__ d_tmax, uint32_t n,
+                                                        uint32_t bits, float ratio, KeyT *__restrict__ keys) {
+    __shared__ uint32_t s_off[kMaxBatchSegments + 1];
+    for (uint32_t k = threadIdx.x; k <= n_segs; k += blockDim.x) s_off[k] = seg_offsets[k];
+    __syncthreads();
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t lo = 0, hi = n_segs;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_off[mid] <= i)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const QuantFrame f = segs[lo].frame;
+    const ulonglong2 *table = reinterpret_cast<const ulonglong2 *>(segs[lo].table);
+    const uint64_t k = ray_key<LAYOUT, TSRC>(f, __ldg(o_tmin + i), __ldg(d_tmax + i), bits, ratio, 0.0f, table);
+    keys[i] = (KeyT)(((uint64_t)lo << bits) | k);
+}
+
+__global__ void batch_frame_kernel(BatchScene *segs, const float *boxes, uint32_t n) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const QuantFrame f = make_frame(boxes + 6 * k, boxes + 6 * k + 3);
+    segs[k].frame = f;
+    segs[k].invE = __fdiv_rn(1.0f, f.E);
 }
 
 template <int LAYOUT, int TSRC>
@@ -155,6 +197,52 @@ static float largest_extent_host(const Box &b) {
         if (x > e) e = x;
     }
     return e;
+}
+
+cudaError_t launch_batch_frames(BatchScene *segs, const float *boxes, uint32_t n, cudaStream_t s) {
+    batch_frame_kernel<<<(n + 127) / 128, 128, 0, s>>>(segs, boxes, n);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+template <int LAYOUT, int TSRC>
+static void launch_keys_batch_t(const BatchScene *segs, const uint32_t *offs, uint32_t n_segs, const float4 *o,
+                                const float4 *d, uint32_t n, uint32_t bits, float ratio, void *keys, bool wide,
+                                cudaStream_t s) {
+    dim3 grid((n + 255) / 256);
+    if (wide)
+        key_batch_kernel<LAYOUT, TSRC, unsigned long long><<<grid, 256, 0, s>>>(
+            segs, offs, n_segs, o, d, n, bits, ratio, static_cast<unsigned long long *>(keys));
+    else
+        key_batch_kernel<LAYOUT, TSRC, uint32_t><<<grid, 256, 0, s>>>(segs, offs, n_segs, o, d, n, bits, ratio,
+                                                                     static_cast<uint32_t *>(keys));
+}
+
+rr_status launch_keys_batch(const BatchScene *segs, const uint32_t *seg_offsets, uint32_t n_segs,
+                            rr_key_layout layout, rr_t_source tsrc, float ratio, uint32_t key_bits,
+                            uint32_t seg_bits, const float *o_tmin, const float *d_tmax, uint32_t n, void *keys,
+                            cudaStream_t s) {
+    if (n == 0) return RR_OK;
+    const bool wide = key_bits + seg_bits > 32;
+    const float4 *o = reinterpret_cast<const float4 *>(o_tmin);
+    const float4 *d = reinterpret_cast<const float4 *>(d_tmax);
+#define RR_KB(L, T) launch_keys_batch_t<L, T>(segs, seg_offsets, n_segs, o, d, n, key_bits, ratio, keys, wide, s)
+    switch (layout) {
+        case RR_KEY_AILA: RR_KB(RR_KEY_AILA, 0); break;
+        case RR_KEY_AILA_COMPACT: RR_KB(RR_KEY_AILA_COMPACT, 0); break;
+        case RR_KEY_ORIGIN: RR_KB(RR_KEY_ORIGIN, 0); break;
+        case RR_KEY_REIS: RR_KB(RR_KEY_REIS, 0); break;
+        case RR_KEY_COSTA: RR_KB(RR_KEY_COSTA, 0); break;
+        case RR_KEY_OCTAHEDRON: RR_KB(RR_KEY_OCTAHEDRON, 0); break;
+        default:
+            if (tsrc == RR_T_ADAPTIVE)
+                RR_KB(RR_KEY_TWO_POINT, RR_T_ADAPTIVE);
+            else
+                RR_KB(RR_KEY_TWO_POINT, RR_T_FIXED);
+    }
+#undef RR_KB
+    note_launches(1);
+    return check_launch("rr_batch keys");
 }
 
 }  // namespace rr

@@ -17,6 +17,7 @@
 #include <chrono>
 #include <cmath>
 
+#include "rr_batch.cuh"
 #include "rr_common.cuh"
 #include "rr_keymath.cuh"
 #include "rr_trace.h"
@@ -25,20 +26,29 @@ namespace rr {
 
 constexpr int kTraceBlock = 256;
 
+// The BVH arrays of one scene.
+struct SceneRef {
+    const float4 *nodes;   // RRNode8 as five float4
+    const float4 *tris;    // RRTri as three float4
+    const float4 *planes;  // two float4 per triangle: normal hi.xyz, lo.x | lo.y, lo.z
+    uint32_t n_nodes;
+};
+
 struct TraceArgs {
-    const float4 *nodes;  // RRNode8 as five float4
-    const float4 *tris;   // RRTri as three float4
-    const float4 *planes; // two float4 per triangle: normal hi.xyz, lo.x | lo.y, lo.z
+    SceneRef scene;  // single-scene kernels
     const float4 *o_tmin;
     const float4 *d_tmax;
     float4 *hits;
     const uint32_t *order;  // NULL: position k traces ray k; else ray order[k]
     uint32_t n;
-    uint32_t n_nodes;
     uint32_t *queue;  // [0] next ray, [1] finished blocks
     uint32_t *err;
     unsigned long long *table;  // length-table cells {sum, count} (accumulating kernel only)
     float tlo[3], thi[3];       // the table's box
+    // batches: ray i belongs to the segment s with seg_offsets[s] <= i < seg_offsets[s + 1]
+    const BatchScene *segs;
+    const uint32_t *seg_offsets;
+    uint32_t n_segs;
 };
 
 __device__ __forceinline__ float safe_inv(float x) {
@@ -62,7 +72,7 @@ __device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
 // stored as hi + lo floats and v0 - o split exactly into hi + lo.  Plain fp32
 // loses relative accuracy when the hit is close to the origin compared with
 // |v0 - o|; this form keeps it at a few ulps.
-__device__ __forceinline__ float refine_t(const TraceArgs &a, uint32_t k, float4 o, float4 d) {
+__device__ __forceinline__ float refine_t(const SceneRef &a, uint32_t k, float4 o, float4 d) {
     const float4 v0 = __ldg(a.tris + 3 * (size_t)k);
     const float4 p0 = __ldg(a.planes + 2 * (size_t)k), p1 = __ldg(a.planes + 2 * (size_t)k + 1);
     const float nh[3] = {p0.x, p0.y, p0.z}, nl[3] = {p0.w, p1.x, p1.y};
@@ -105,7 +115,7 @@ struct RayState {
     int sp;
 };
 
-__device__ __forceinline__ void ray_begin(RayState &r, const TraceArgs &a, float4 o, float4 d) {
+__device__ __forceinline__ void ray_begin(RayState &r, const SceneRef &a, float4 o, float4 d) {
     r.o = o;
     r.d = d;
     r.idx = safe_inv(d.x);
@@ -144,7 +154,7 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
 // Node part of a traversal round: visit the nearest node of the current group
 // (its hit inner children become the current group, its hit leaves the
 // pending triangle group).
-__device__ __forceinline__ bool ray_visit_node(RayState &r, uint2 *stack, const TraceArgs &a) {
+__device__ __forceinline__ bool ray_visit_node(RayState &r, uint2 *stack, const SceneRef &a) {
     const float tmin = r.o.w;
     const uint32_t pos = __ffs(r.g_hits) - 1u;
     r.g_hits &= r.g_hits - 1u;
@@ -228,7 +238,7 @@ __device__ __forceinline__ bool ray_visit_node(RayState &r, uint2 *stack, const 
 // Tests every triangle of the pending group.  ANY: the first hit ends the ray
 // (the pending group, the current node group and the stack are dropped).
 template <bool ANY>
-__device__ __forceinline__ void ray_test_triangles(RayState &r, const TraceArgs &a) {
+__device__ __forceinline__ void ray_test_triangles(RayState &r, const SceneRef &a) {
     const float tmin = r.o.w;
     while (r.t_hits != 0u) {
         const uint32_t b = __ffs(r.t_hits) - 1u;
@@ -268,7 +278,7 @@ __device__ __forceinline__ void ray_test_triangles(RayState &r, const TraceArgs 
     }
 }
 
-__device__ __forceinline__ float4 ray_result(const RayState &r, const TraceArgs &a) {
+__device__ __forceinline__ float4 ray_result(const RayState &r, const SceneRef &a) {
     if (r.best_tri == kMiss) return make_float4(__int_as_float(0x7f800000), 0.0f, 0.0f, __uint_as_float(kMiss));
     const float tr = refine_t(a, r.best_k, r.o, r.d);
     return make_float4(isfinite(tr) ? tr : r.best, r.bu, r.bv, __uint_as_float(r.best_tri));
@@ -281,8 +291,8 @@ constexpr uint32_t kQueueBatch = 32;
 // The length-table update of one traced ray (Section 3.1.6), the arithmetic of
 // table_accumulate_kernel: a ray that hit adds trunc(clamp(t*|d|/E, 0, 64)*2^24)
 // and one count to the cell of its 20-bit compacted Aila code.
-__device__ __forceinline__ void accumulate_hit(const TraceArgs &a, const QuantFrame &f, float invE, float4 o,
-                                               float4 d, float4 h) {
+__device__ __forceinline__ void accumulate_hit(unsigned long long *table, const QuantFrame &f, float invE,
+                                               float4 o, float4 d, float4 h) {
     if (__float_as_uint(h.w) == kMiss || !isfinite(h.x)) return;
     uint32_t qo[3], qd[3];
     float dh[3];
@@ -291,19 +301,26 @@ __device__ __forceinline__ void accumulate_hit(const TraceArgs &a, const QuantFr
     float x = __fmul_rn(__fmul_rn(h.x, length3(d.x, d.y, d.z)), invE);
     if (!(x > 0.0f)) x = 0.0f;
     if (x > 64.0f) x = 64.0f;
-    atomicAdd(a.table + 2 * (size_t)cell, (unsigned long long)__float2uint_rz(__fmul_rn(x, 16777216.0f)));
-    atomicAdd(a.table + 2 * (size_t)cell + 1, 1ull);
+    atomicAdd(table + 2 * (size_t)cell, (unsigned long long)__float2uint_rz(__fmul_rn(x, 16777216.0f)));
+    atomicAdd(table + 2 * (size_t)cell + 1, 1ull);
 }
 
-template <bool ACCUM, bool ANY>
-__global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceArgs a) {
+// MULTI: rays of several scenes in one launch (a batch); each lane finds the
+// segment of its ray and traces that segment's BVH (and updates its table).
+template <bool ACCUM, bool ANY, bool MULTI, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) trace_kernel(TraceArgs a) {
+    __shared__ uint32_t s_off[MULTI ? kMaxBatchSegments + 1 : 1];
     const uint32_t lane = threadIdx.x & 31u;
     uint2 stack[kTraceStack];
-    QuantFrame f;
-    float invE = 0.0f;
-    if (ACCUM) {
-        f = make_frame(a.tlo, a.thi);
-        invE = __fdiv_rn(1.0f, f.E);
+    QuantFrame f0;
+    float invE0 = 0.0f;
+    if (ACCUM && !MULTI) {
+        f0 = make_frame(a.tlo, a.thi);
+        invE0 = __fdiv_rn(1.0f, f0.E);
+    }
+    if (MULTI) {
+        for (uint32_t k = threadIdx.x; k <= a.n_segs; k += BLOCK) s_off[k] = a.seg_offsets[k];
+        __syncthreads();
     }
     while (true) {
         uint32_t base = 0;
@@ -319,16 +336,42 @@ __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceArgs a) {
                 atomicOr(a.err, RR_DEVERR_BAD_INDEX);
                 continue;
             }
+            SceneRef sc = a.scene;
+            unsigned long long *table = a.table;
+            QuantFrame f = f0;
+            float invE = invE0;
+            if (MULTI) {
+                // the last segment starting at or before i (empty segments share
+                // their start with the next one, which wins)
+                uint32_t lo = 0, hi = a.n_segs;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (s_off[mid] <= i)
+                        lo = mid;
+                    else
+                        hi = mid;
+                }
+                const BatchScene *bs = a.segs + lo;
+                sc.nodes = bs->nodes;
+                sc.tris = bs->tris;
+                sc.planes = bs->planes;
+                sc.n_nodes = bs->n_nodes;
+                if (ACCUM) {
+                    table = bs->table;
+                    f = bs->frame;
+                    invE = bs->invE;
+                }
+            }
             RayState r;
             const float4 o = __ldg(a.o_tmin + i), d = __ldg(a.d_tmax + i);
-            ray_begin(r, a, o, d);
+            ray_begin(r, sc, o, d);
             while (true) {
-                if (r.g_hits != 0u && !ray_visit_node(r, stack, a)) {
+                if (r.g_hits != 0u && !ray_visit_node(r, stack, sc)) {
                     atomicOr(a.err, RR_DEVERR_TRACE_STACK);
                     r.best_tri = kMiss;
                     break;
                 }
-                ray_test_triangles<ANY>(r, a);
+                ray_test_triangles<ANY>(r, sc);
                 if (r.g_hits == 0u) {
                     if (r.sp == 0) break;
                     const uint2 e = stack[--r.sp];
@@ -337,9 +380,9 @@ __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceArgs a) {
                     r.g_imask = (e.y >> 8) & 0xFFu;
                 }
             }
-            const float4 h = ray_result(r, a);
+            const float4 h = ray_result(r, sc);
             a.hits[i] = h;
-            if (ACCUM) accumulate_hit(a, f, invE, o, d, h);
+            if (ACCUM && table) accumulate_hit(table, f, invE, o, d, h);
         }
     }
     __syncthreads();
@@ -433,15 +476,24 @@ extern "C" rr_status rr_bvh_get_info(const rr_bvh *b, rr_bvh_info *info) {
 
 namespace {
 
-template <bool ACC, bool ANY>
+template <bool ACC, bool ANY, bool MULTI, int BLOCK>
 int trace_blocks_per_sm() {
     static int bps = 0;
     if (bps == 0) {
         int v = 0;
-        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, trace_kernel<ACC, ANY>, kTraceBlock, 0);
+        const cudaError_t e =
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, trace_kernel<ACC, ANY, MULTI, BLOCK>, BLOCK, 0);
         bps = (e != cudaSuccess || v < 1) ? 1 : v;
     }
     return bps;
+}
+
+template <bool ACC, bool ANY, bool MULTI, int BLOCK>
+void trace_enqueue(const TraceArgs &a, int sm_count, cudaStream_t s) {
+    const uint32_t want = (a.n + kQueueBatch - 1) / kQueueBatch;  // warps that can get work
+    uint32_t grid = (uint32_t)sm_count * (uint32_t)trace_blocks_per_sm<ACC, ANY, MULTI, BLOCK>();
+    grid = std::max(1u, std::min(grid, (want + BLOCK / 32 - 1) / (BLOCK / 32)));
+    trace_kernel<ACC, ANY, MULTI, BLOCK><<<grid, BLOCK, 0, s>>>(a);
 }
 
 rr_status launch_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax, const uint32_t *order, uint32_t n,
@@ -461,19 +513,17 @@ rr_status launch_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax
     rr_status st;
     DeviceState *ds = device_state(&st);
     if (!ds) return st;
-    const int bps = table ? trace_blocks_per_sm<true, false>()
-                          : (any ? trace_blocks_per_sm<false, true>() : trace_blocks_per_sm<false, false>());
     const uint32_t slot = ds->next_counter.fetch_add(1) % (kCounterPool / 2);
-    TraceArgs a;
-    a.nodes = reinterpret_cast<const float4 *>(b->nodes);
-    a.tris = reinterpret_cast<const float4 *>(b->tris);
-    a.planes = b->planes;
+    TraceArgs a{};
+    a.scene.nodes = reinterpret_cast<const float4 *>(b->nodes);
+    a.scene.tris = reinterpret_cast<const float4 *>(b->tris);
+    a.scene.planes = b->planes;
+    a.scene.n_nodes = b->n_nodes;
     a.o_tmin = reinterpret_cast<const float4 *>(o_tmin);
     a.d_tmax = reinterpret_cast<const float4 *>(d_tmax);
     a.hits = reinterpret_cast<float4 *>(hits_out);
     a.order = order;
     a.n = n;
-    a.n_nodes = b->n_nodes;
     a.queue = ds->counters + 2 * slot;
     a.err = ds->err;
     a.table = table ? table->cells : nullptr;
@@ -481,21 +531,53 @@ rr_status launch_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax
         a.tlo[c] = table ? table->box.lo[c] : 0.0f;
         a.thi[c] = table ? table->box.hi[c] : 0.0f;
     }
-    const uint32_t want = (n + kQueueBatch - 1) / kQueueBatch;  // warps that can get work
-    uint32_t grid = (uint32_t)ds->sm_count * (uint32_t)bps;
-    grid = std::max(1u, std::min(grid, (want + kTraceBlock / 32 - 1) / (kTraceBlock / 32)));
     cudaStream_t s = as_stream(stream);
     if (table)
-        trace_kernel<true, false><<<grid, kTraceBlock, 0, s>>>(a);
+        trace_enqueue<true, false, false, kTraceBlock>(a, ds->sm_count, s);
     else if (any)
-        trace_kernel<false, true><<<grid, kTraceBlock, 0, s>>>(a);
+        trace_enqueue<false, true, false, kTraceBlock>(a, ds->sm_count, s);
     else
-        trace_kernel<false, false><<<grid, kTraceBlock, 0, s>>>(a);
+        trace_enqueue<false, false, false, kTraceBlock>(a, ds->sm_count, s);
     note_launches(1);
     return check_launch(what);
 }
 
 }  // namespace
+
+namespace rr {
+
+rr_status launch_trace_batch(const BatchScene *segs, const uint32_t *seg_offsets, uint32_t n_segs, const float *o_tmin,
+                             const float *d_tmax, const uint32_t *order, uint32_t n, float *hits_out,
+                             bool accumulate, uint32_t block, uint32_t *queue, cudaStream_t s) {
+    rr_status st;
+    DeviceState *ds = device_state(&st);
+    if (!ds) return st;
+    TraceArgs a{};
+    a.o_tmin = reinterpret_cast<const float4 *>(o_tmin);
+    a.d_tmax = reinterpret_cast<const float4 *>(d_tmax);
+    a.hits = reinterpret_cast<float4 *>(hits_out);
+    a.order = order;
+    a.n = n;
+    a.queue = queue;
+    a.err = ds->err;
+    a.segs = segs;
+    a.seg_offsets = seg_offsets;
+    a.n_segs = n_segs;
+    const int sms = ds->sm_count;
+    if (accumulate) {
+        if (block == 128) trace_enqueue<true, false, true, 128>(a, sms, s);
+        else if (block == 512) trace_enqueue<true, false, true, 512>(a, sms, s);
+        else trace_enqueue<true, false, true, 256>(a, sms, s);
+    } else {
+        if (block == 128) trace_enqueue<false, false, true, 128>(a, sms, s);
+        else if (block == 512) trace_enqueue<false, false, true, 512>(a, sms, s);
+        else trace_enqueue<false, false, true, 256>(a, sms, s);
+    }
+    note_launches(1);
+    return check_launch("rr_batch trace");
+}
+
+}  // namespace rr
 
 extern "C" rr_status rr_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax, uint32_t n, float *hits_out,
                               void *stream) {

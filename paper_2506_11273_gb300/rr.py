@@ -47,7 +47,8 @@ EXPORTS = [
     "rr_length_table_write", "rr_length_table_destroy", "rr_pipeline_create",
     "rr_pipeline_destroy", "rr_pipeline_run", "rr_pipeline_run_host", "rr_device_error",
     "rr_status_string", "rr_last_error_message", "rr_kernel_launch_count", "rr_sort_noalloc",
-    "rr_coherence_capsule", "rr_trace_ex", "rr_sort_segments",
+    "rr_coherence_capsule", "rr_trace_ex", "rr_sort_segments", "rr_batch_create", "rr_batch_destroy",
+    "rr_batch_info", "rr_batch_run", "rr_batch_run_loop", "rr_batch_tune",
 ]
 
 
@@ -61,6 +62,18 @@ class KeyParams(C.Structure):
     _fields_ = [("layout", C.c_uint32), ("bits", C.c_uint32), ("t_source", C.c_uint32),
                 ("ratio", C.c_float), ("aabb_lo", C.c_float * 3), ("aabb_hi", C.c_float * 3),
                 ("t_given", C.c_void_p), ("table", C.c_void_p)]
+
+
+class Wavefront(C.Structure):
+    _fields_ = [("bvh", C.c_void_p), ("table", C.c_void_p), ("aabb_lo", C.c_float * 3),
+                ("aabb_hi", C.c_float * 3), ("offset", C.c_uint32), ("count", C.c_uint32)]
+
+
+class BatchConfig(C.Structure):
+    _fields_ = [("key_bits", C.c_uint32), ("radix_bits", C.c_uint32), ("trace_block", C.c_uint32)]
+
+    def as_tuple(self):
+        return (int(self.key_bits), int(self.radix_bits), int(self.trace_block))
 
 
 class BvhInfo(C.Structure):
@@ -102,6 +115,12 @@ def lib():
             L.rr_pipeline_run_host.argtypes = [vp, vp, vp, vp, u32, vp, vp, vp]
             L.rr_sort_segments.argtypes = [vp, vp, vp, u32, u32, u32, vp]
             L.rr_trace_ex.argtypes = [vp, vp, vp, vp, u32, vp, u32, vp, vp]
+            L.rr_batch_create.argtypes = [C.POINTER(Wavefront), u32, u32, u32, C.c_float, C.POINTER(vp)]
+            L.rr_batch_destroy.argtypes = [vp]
+            L.rr_batch_info.argtypes = [vp, C.POINTER(u32), C.POINTER(u32), C.POINTER(u32)]
+            L.rr_batch_run.argtypes = [vp, vp, vp, vp, vp, C.POINTER(BatchConfig), vp]
+            L.rr_batch_run_loop.argtypes = [vp, vp, vp, vp, vp, C.POINTER(BatchConfig), vp]
+            L.rr_batch_tune.argtypes = [vp, vp, vp, vp, C.POINTER(BatchConfig), C.POINTER(C.c_float), vp]
             L.rr_coherence_capsule.argtypes = [vp, vp, vp, u32, u32, C.c_float, vp, vp]
             L.rr_device_error.argtypes = [C.POINTER(C.c_uint32)]
             L.rr_status_string.argtypes = [i32]
@@ -358,6 +377,72 @@ class Pipeline:
     def close(self):
         if getattr(self, "handle", None):
             lib().rr_pipeline_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- batched execution
+
+class Batch:
+    """Owner of an rr_batch: wavefronts over resident scenes, run as one graph.
+
+    fronts: list of (bvh: BVH, table: LengthTable | None, aabb_lo, aabb_hi, count);
+    offsets follow from the counts (contiguous, in order)."""
+
+    def __init__(self, fronts, layout: int, t_source: int = RR_T_FIXED, ratio: float = 0.25):
+        arr = (Wavefront * len(fronts))()
+        off = 0
+        self._keep = []
+        for k, (bvh, table, lo, hi, count) in enumerate(fronts):
+            w = arr[k]
+            w.bvh = bvh.handle
+            w.table = table.handle if table is not None else None
+            for c in range(3):
+                w.aabb_lo[c] = float(lo[c])
+                w.aabb_hi[c] = float(hi[c])
+            w.offset = off
+            w.count = int(count)
+            off += int(count)
+            self._keep.append((bvh, table))
+        self.n = off
+        self.offsets = [w.offset for w in arr] + [off]
+        h = C.c_void_p()
+        _check(lib().rr_batch_create(arr, len(fronts), layout, t_source, float(np.float32(ratio)), C.byref(h)),
+               "rr_batch_create")
+        self.handle = h
+
+    def info(self):
+        n, sb, g = C.c_uint32(), C.c_uint32(), C.c_uint32()
+        _check(lib().rr_batch_info(self.handle, C.byref(n), C.byref(sb), C.byref(g)), "rr_batch_info")
+        return dict(n_rays=n.value, seg_bits=sb.value, graphs=g.value)
+
+    @staticmethod
+    def config(key_bits: int, radix_bits: int = 8, trace_block: int = 256) -> BatchConfig:
+        return BatchConfig(key_bits, radix_bits, trace_block)
+
+    def run(self, o_tmin, d_tmax, hits_out, cfg: BatchConfig, perm_out=None, stream=None):
+        _check(lib().rr_batch_run(self.handle, _ptr(o_tmin), _ptr(d_tmax), _ptr(hits_out), _ptr(perm_out),
+                                  C.byref(cfg), _stream(stream)), "rr_batch_run")
+
+    def run_loop(self, o_tmin, d_tmax, hits_out, cfg: BatchConfig, perm_out=None, stream=None):
+        _check(lib().rr_batch_run_loop(self.handle, _ptr(o_tmin), _ptr(d_tmax), _ptr(hits_out),
+                                       _ptr(perm_out), C.byref(cfg), _stream(stream)), "rr_batch_run_loop")
+
+    def tune(self, o_tmin, d_tmax, hits_out, stream=None):
+        best = BatchConfig()
+        ms = C.c_float()
+        _check(lib().rr_batch_tune(self.handle, _ptr(o_tmin), _ptr(d_tmax), _ptr(hits_out), C.byref(best),
+                                   C.byref(ms), _stream(stream)), "rr_batch_tune")
+        return best, float(ms.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rr_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
