@@ -471,7 +471,10 @@ def bench_batched(args, dev, flush):
     hits = torch.empty(n, 4, device=dev)
     perm = torch.empty(n, dtype=torch.int32, device=dev)
     t0 = time.time()
-    cfg, tuned_ms = batch.tune(o, d, hits)
+    tuned, tuned_ms = batch.tune(o, d, hits)
+    # the reordered batch: the tuner's choice, or the best sorted candidate
+    # when the tuner found that not reordering was faster
+    cfg = tuned if tuned.key_bits else rr.Batch.config(24, 8, tuned.trace_block)
     tune_s = time.time() - t0
     stream = torch.cuda.current_stream()
 
@@ -503,18 +506,23 @@ def bench_batched(args, dev, flush):
             a, b_ = offs[k], offs[k + 1]
             rr.rr_trace(fronts[k][0], o[a:b_], d[a:b_], hits[a:b_])
     ms_uns = timed(unsorted, K)
+    cfg0 = rr.Batch.config(0, 8, cfg.trace_block)
+    ms_graph0 = timed(lambda: batch.run(o, d, hits, cfg0), K)
     if rr.rr_device_error() != 0:
         raise RuntimeError("device error flag set during the batched measurement")
     out = {"workload": "%d wavefronts of log-uniform %d-%d rays over %d scenes of %s triangles; Two Point "
                        "key (fixed estimate)" % (BATCH_WAVEFRONTS, int(1e4 * scale), int(2e6 * scale),
                                                  len(scenes), "/".join(str(t.shape[0]) for t in scenes)),
-           "rays": int(n), "autotuned": {"key_bits": cfg.key_bits, "radix_bits": cfg.radix_bits,
-                                          "trace_block": cfg.trace_block, "tuned_ms": round(tuned_ms, 3),
+           "rays": int(n), "autotuned": {"key_bits": tuned.key_bits, "radix_bits": tuned.radix_bits,
+                                          "trace_block": tuned.trace_block, "tuned_ms": round(tuned_ms, 3),
                                           "tune_s": round(tune_s, 2)},
+           "sorted_config": {"key_bits": cfg.key_bits, "radix_bits": cfg.radix_bits,
+                             "trace_block": cfg.trace_block},
            "graph_ms": round(ms_graph, 3), "graph_mrays": round(n / (ms_graph * 1e-3) / 1e6, 1),
            "graph_kernels": 3 + -(-(cfg.key_bits + batch.info()["seg_bits"]) // cfg.radix_bits),
            "loop_ms": round(ms_loop, 3), "loop_mrays": round(n / (ms_loop * 1e-3) / 1e6, 1),
            "loop_launches": int(loop_launches),
+           "unsorted_graph_ms": round(ms_graph0, 3), "unsorted_graph_mrays": round(n / (ms_graph0 * 1e-3) / 1e6, 1),
            "unsorted_loop_ms": round(ms_uns, 3), "unsorted_loop_mrays": round(n / (ms_uns * 1e-3) / 1e6, 1)}
     batch.close()
     return out

@@ -377,7 +377,9 @@ typedef struct {
 } rr_wavefront;
 
 typedef struct {
-    uint32_t key_bits;     /* bits of each wavefront's own key; key_bits + wavefront bits <= 64 */
+    uint32_t key_bits;     /* bits of each wavefront's own key; key_bits + wavefront bits <= 64.
+                              0: no reordering (rays traced in input order, no keys, no sort,
+                              perm_out not written) */
     uint32_t radix_bits;   /* 4 or 8 */
     uint32_t trace_block;  /* threads per trace block: 128, 256 or 512 */
 } rr_batch_config;
@@ -423,7 +425,8 @@ rr_status rr_batch_run_loop(rr_batch *batch, const float *o_tmin, const float *d
 /*
  * rr_batch_tune - autotuner: times rr_batch_run on these buffers for key bits
  * {12, 16, 20, 24, 32, 48, 64} (capped by the wavefront bits) x radix width {4, 8}
- * at 256-thread trace blocks, then trace blocks of 128 and 512 for the winner,
+ * and for no reordering (key bits 0) at 256-thread trace blocks, then trace
+ * blocks of 128 and 512 for the winner,
  * and returns the fastest configuration (mean of 3 timed runs after one
  * warm-up) and its time.  Length tables are saved before and restored after,
  * so tuning leaves them as it found them.  Synchronising.

@@ -34,7 +34,7 @@ uint32_t bits_for(uint32_t n) {  // bits that number 0..n-1
 }
 
 bool config_ok(const rr_batch_config *c, uint32_t seg_bits) {
-    return c && c->key_bits >= 1 && c->key_bits + seg_bits <= 64 && (c->radix_bits == 4 || c->radix_bits == 8) &&
+    return c && c->key_bits + seg_bits <= 64 && (c->radix_bits == 4 || c->radix_bits == 8) &&
            (c->trace_block == 128 || c->trace_block == 256 || c->trace_block == 512);
 }
 
@@ -72,6 +72,9 @@ bool accumulating(const rr_batch *b) { return b->layout == RR_KEY_TWO_POINT && b
 // The whole chain on one stream: keys, sort, trace.
 rr_status enqueue_batch(rr_batch *b, const float *o, const float *d, float *hits, uint32_t *perm,
                         const rr_batch_config &c, cudaStream_t s) {
+    if (c.key_bits == 0)  // no reordering: every ray traced in input order
+        return launch_trace_batch(b->d_segs, b->d_offsets, b->n_fronts, o, d, nullptr, b->n_total, hits,
+                                  accumulating(b), c.trace_block, b->queue, s);
     rr_status st = launch_keys_batch(b->d_segs, b->d_offsets, b->n_fronts, b->layout, b->tsrc, b->ratio, c.key_bits,
                                      b->seg_bits, o, d, b->n_total, b->keys, s);
     if (st != RR_OK) return st;
@@ -276,6 +279,16 @@ extern "C" rr_status rr_batch_run_loop(rr_batch *b, const float *o_tmin, const f
     uint32_t *perm = perm_out ? perm_out : b->perm;
     const size_t kb = cfg->key_bits > 32 ? 8 : 4;
     unsigned char *keys = static_cast<unsigned char *>(b->keys);
+    if (cfg->key_bits == 0) {
+        for (uint32_t k = 0; k < b->n_fronts; ++k) {
+            const rr_wavefront &f = b->fronts[k];
+            if (f.count == 0) continue;
+            st = rr_trace_ex(f.bvh, o_tmin + 4ull * f.offset, d_tmax + 4ull * f.offset, nullptr, f.count,
+                             hits_out + 4ull * f.offset, 0u, accumulating(b) ? f.table : nullptr, stream);
+            if (st != RR_OK) return st;
+        }
+        return RR_OK;
+    }
     // as in the graph: every key is computed before any trace updates a table
     for (uint32_t k = 0; k < b->n_fronts; ++k) {
         const rr_wavefront &f = b->fronts[k];
@@ -352,19 +365,21 @@ extern "C" rr_status rr_batch_tune(rr_batch *b, const float *o_tmin, const float
         *ms = tot / reps;
         return RR_OK;
     };
-    // key bits x radix width at the default block, then the block for the winner
-    const uint32_t cand_bits[] = {12, 16, 20, 24, 32, 48, 64};
+    // key bits x radix width at the default block (0 bits: no reordering), then
+    // the block for the winner
+    const uint32_t cand_bits[] = {0, 12, 16, 20, 24, 32, 48, 64};
     rr_batch_config win{0, 0, 0};
-    float win_ms = 0.0f;
+    float win_ms = -1.0f;
     st = RR_OK;
     for (uint32_t kb : cand_bits) {
         const uint32_t bits = std::min(kb, 64u - b->seg_bits);
         for (uint32_t rb : {4u, 8u}) {
+            if (kb == 0 && rb == 4) continue;  // nothing is sorted
             const rr_batch_config c{bits, rb, 256};
             float ms = 0.0f;
             st = time_cfg(c, &ms);
             if (st != RR_OK) break;
-            if (win.key_bits == 0 || ms < win_ms) {
+            if (win_ms < 0.0f || ms < win_ms) {
                 win = c;
                 win_ms = ms;
             }
