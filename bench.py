@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--small", action="store_true", help="tiny scene and wavefront (for profiling runs)")
     ap.add_argument("--no-extra", action="store_true", help="skip the per-bounce and e2e sweeps")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-execution measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     return ap.parse_args()
 
 
@@ -420,6 +421,12 @@ def run_ours(args):
     out.update(extra)
     if not args.no_batched:
         out["batched"] = bench_batched(args, dev, flush)
+    if not args.no_serving:
+        out["serving"] = bench_serving(args, dev)
+        mid = out["serving"]["loads"][-1]
+        out["p99_latency_ms"] = mid["p99_ms"]
+        out["p99_at_load"] = "%.0f%% of measured capacity (%.1f requests/s)" % (100 * mid["load_frac"],
+                                                                                mid["offered_rps"])
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline(tris, lo, hi, sample=20000 if args.small else 100000)
         print(json.dumps(out), flush=True)
@@ -526,6 +533,105 @@ def bench_batched(args, dev, flush):
            "unsorted_loop_ms": round(ms_uns, 3), "unsorted_loop_mrays": round(n / (ms_uns * 1e-3) / 1e6, 1)}
     batch.close()
     return out
+
+
+# ----------------------------------------------------------------------------- serving
+
+# 8 resident scenes of 50k..4M triangles built like the path-tracer scene
+SERVE_SCENES = [(112, 200, 417), (158, 316, 833), (237, 475, 2083), (335, 670, 4167), (474, 949, 8333),
+                (671, 1341, 16667), (822, 1643, 25000), (949, 1897, 33333)]
+SERVE_BUDGET = 120 << 30
+SERVE_POOL = 1 << 18    # distinct rays generated per scene and kind (requests tile them)
+SERVE_MAX_REQ = 4 << 20
+
+
+def bench_serving(args, dev):
+    """Poisson arrivals of requests of log-uniform 4k-4M rays (60% diffuse, 40%
+    glossy) over 8 resident scenes, served with continuous batching under a
+    120 GB budget; p50/p99 latency and throughput at several offered loads."""
+    import threading
+
+    import torch
+
+    from paper_2506_11273_gb300 import rr
+    from paper_2506_11273_gb300 import workloads as W
+
+    small = args.small
+    scale = 0.05 if small else 1.0
+    lo_n, hi_n = int(4096 * scale) + 1, int(SERVE_MAX_REQ * scale)
+    pool_n = max(1024, int(SERVE_POOL * scale))
+    srv = rr.Server(budget_bytes=SERVE_BUDGET, slots=4, max_batch_rays=1 << 25, key_bits=24, radix_bits=8,
+                    trace_block=128)
+    scenes = []
+    pools = {}
+    t0 = time.time()
+    for k, (cx, cz, nb) in enumerate(SERVE_SCENES):
+        if small:
+            cx, cz, nb = max(8, cx // 8), max(16, cz // 8), max(10, nb // 64)
+        tris = W.scene_terrain(seed=60 + k, cells_x=cx, cells_z=cz, n_boxes=nb)
+        bvh = rr.BVH(tris)
+        lo, hi = W.scene_aabb(tris)
+        sid = srv.add_scene(bvh, lo, hi)
+        scenes.append((bvh, tris.shape[0]))
+        for kind in ("diffuse", "glossy"):
+            r = W.request_rays(tris, pool_n, kind, seed=700 + 2 * k + (kind == "glossy"))
+            reps = -(-hi_n // pool_n)
+            o = torch.from_numpy(np.tile(r.o_tmin, (reps, 1))).pin_memory()
+            d = torch.from_numpy(np.tile(r.d_tmax, (reps, 1))).pin_memory()
+            pools[(sid, kind)] = (o, d)
+    setup_s = time.time() - t0
+    hits_sink = torch.empty(hi_n, 4).pin_memory()  # results are written here and not read
+
+    def run_load(rate_rps, duration_s, seed):
+        rng = np.random.default_rng(seed)
+        n_req = max(8, int(rate_rps * duration_s))
+        gaps = rng.exponential(1.0 / rate_rps, n_req)
+        sizes = np.exp(rng.uniform(np.log(lo_n), np.log(hi_n), n_req)).astype(np.int64)
+        which = rng.integers(0, len(scenes), n_req)
+        kinds = np.where(rng.random(n_req) < 0.6, "diffuse", "glossy")
+        tickets = []
+        start = time.perf_counter()
+        t_next = start
+        for k in range(n_req):
+            t_next += gaps[k]
+            while True:
+                dt = t_next - time.perf_counter()
+                if dt <= 0:
+                    break
+                time.sleep(min(dt, 0.0005))
+            o, d = pools[(int(which[k]), str(kinds[k]))]
+            tickets.append((srv.submit(int(which[k]), o, d, hits_sink, n=int(sizes[k])), int(sizes[k])))
+        lat, rays, first, last = [], 0, None, None
+        for t, n in tickets:
+            tm = srv.wait(t)
+            lat.append((tm["done_ns"] - tm["submit_ns"]) * 1e-6)
+            rays += n
+            first = tm["submit_ns"] if first is None else min(first, tm["submit_ns"])
+            last = tm["done_ns"] if last is None else max(last, tm["done_ns"])
+        span = (last - first) * 1e-9
+        lat = np.array(lat)
+        return {"offered_rps": round(rate_rps, 1), "offered_mrays": round(rate_rps * float(np.mean(sizes)) / 1e6, 1),
+                "requests": n_req, "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(lat.mean()), 3),
+                "throughput_mrays": round(rays / span / 1e6, 1)}
+
+    # capacity: a burst of requests all at once
+    mean_n = (hi_n - lo_n) / np.log(hi_n / lo_n)
+    burst = run_load(1e6, 64 / 1e6, seed=1)
+    cap_mrays = burst["throughput_mrays"]
+    cap_rps = cap_mrays * 1e6 / mean_n
+    loads = []
+    for frac in (0.25, 0.5, 0.75, 0.9):
+        loads.append(dict(run_load(frac * cap_rps, 1.5 if not small else 0.5, seed=int(frac * 100)),
+                          load_frac=frac))
+    st = srv.stats()
+    srv.close()
+    return {"workload": "Poisson arrivals of log-uniform %d-%d-ray requests (60%% diffuse, 40%% glossy) over 8 "
+                        "scenes of %s triangles; budget %d GB, 4 stream slots, Two Point key 24 bits" %
+                        (lo_n, hi_n, "/".join(str(n) for _, n in scenes), SERVE_BUDGET >> 30),
+            "capacity_mrays": cap_mrays, "loads": loads, "setup_s": round(setup_s, 1),
+            "batches": st["batches"], "max_batch_requests": st["max_batch_requests"],
+            "peak_reserved_gb": round(st["peak_reserved_bytes"] / 2**30, 2)}
 
 
 # ----------------------------------------------------------------------------- oracle

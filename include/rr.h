@@ -434,6 +434,83 @@ rr_status rr_batch_run_loop(rr_batch *batch, const float *o_tmin, const float *d
 rr_status rr_batch_tune(rr_batch *batch, const float *o_tmin, const float *d_tmax, float *hits_out,
                         rr_batch_config *best, float *best_ms, void *stream);
 
+/* ---------------------------------------------------------------- serving */
+
+/*
+ * A server answers ray-batch requests (host buffers in, closest hits out)
+ * against resident scenes.  A worker thread owned by the server admits the
+ * requests that have arrived, in arrival order, as far as a free stream slot
+ * and the device-memory budget allow, and runs each admitted group as one
+ * multi-scene batch (the rr_batch chain: keys in each request's own box, one
+ * stable sort with the request number above the key bits, one trace through
+ * the permutation) between its copy-in and copy-out, on the slot's stream.
+ * Groups on different slots overlap on the device, and requests that arrive
+ * meanwhile join the next group (continuous batching).  A request's hits do
+ * not depend on which other requests share its group: each ray's closest hit
+ * is computed by the same arithmetic whatever the order.
+ */
+typedef struct {
+    uint64_t budget_bytes;     /* device memory the admitted requests may hold at once */
+    uint32_t slots;            /* concurrent groups (streams), 1..64 */
+    uint32_t max_batch_rays;   /* rays per group, and the largest request accepted */
+    uint32_t layout;           /* rr_key_layout of every request */
+    uint32_t t_source;         /* rr_t_source (Two Point; GIVEN is not served) */
+    float ratio;               /* FIXED estimate ratio */
+    uint32_t key_bits;         /* bits of each request's own key (capped at 64 - request bits) */
+    uint32_t radix_bits;       /* 4 or 8 */
+    uint32_t trace_block;      /* 128, 256 or 512 */
+} rr_server_config;
+
+typedef struct {
+    uint64_t submit_ns;        /* steady-clock times: submission, */
+    uint64_t start_ns;         /* admission (group enqueued), */
+    uint64_t done_ns;          /* copy-out finished (host function ran) */
+    uint32_t batch_requests;   /* requests in the group that carried this one */
+} rr_request_times;
+
+typedef struct {
+    uint64_t batches;             /* groups run so far */
+    uint64_t max_batch_requests;  /* largest group */
+    uint64_t peak_reserved_bytes; /* most device memory admitted at once */
+    uint64_t reserved_bytes;      /* device memory admitted now */
+    uint64_t waiting;             /* requests not yet admitted */
+} rr_server_stats_t;
+
+typedef struct rr_server rr_server;
+
+/* Starts the worker thread; the current device is the server's. */
+rr_status rr_server_create(const rr_server_config *cfg, rr_server **out);
+
+/*
+ * Makes a scene resident: its BVH (which must outlive the server), the box its
+ * keys are quantised in, and for Two Point ADAPTIVE its length table (read by
+ * the keys and updated by the trace of every request on the scene).
+ */
+rr_status rr_server_add_scene(rr_server *srv, const rr_bvh *bvh, rr_length_table *table,
+                              const float aabb_lo[3], const float aabb_hi[3], uint32_t *scene_id);
+
+/*
+ * Queues a request of n rays (host float4 o_tmin and d_tmax; hits_host
+ * receives n float4 hits in input order).  The buffers must stay valid and
+ * untouched until rr_server_wait returns for the ticket; pinned host memory
+ * lets the copies run asynchronously.  Returns at once.  A request whose
+ * memory alone exceeds the budget is refused (RR_ERR_INVALID_ARG).
+ */
+rr_status rr_server_submit(rr_server *srv, uint32_t scene_id, const float *o_tmin_host,
+                           const float *d_tmax_host, uint32_t n, float *hits_host, uint64_t *ticket);
+
+/*
+ * Blocks until the request is finished (its hits are in hits_host) or
+ * timeout_s passes (RR_ERR_TIMEOUT, the ticket stays valid).  On return the
+ * ticket is released; times (may be NULL) receives its timestamps.
+ */
+rr_status rr_server_wait(rr_server *srv, uint64_t ticket, double timeout_s, rr_request_times *times);
+
+rr_status rr_server_stats(rr_server *srv, rr_server_stats_t *out);
+
+/* Finishes every queued request, stops the worker and frees the server. */
+rr_status rr_server_destroy(rr_server *srv);
+
 /* ---------------------------------------------------------------- diagnostics */
 
 /* Reads and clears the current device's error word (RR_DEVERR_* flags); synchronising. */

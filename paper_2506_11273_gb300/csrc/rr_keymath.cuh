@@ -48,7 +48,7 @@ __device__ __forceinline__ float length3(float x, float y, float z) {
 }
 
 // Spreads the low 11 bits of x so that bit i lands on bit 6i.
-__device__ __forceinline__ uint64_t spread6(uint64_t x) {
+__host__ __device__ __forceinline__ uint64_t spread6(uint64_t x) {
     x &= 0x7FFull;
     x = (x | (x << 40)) & 0x00070000000000FFull;
     x = (x | (x << 20)) & 0x000700000F00000Full;
@@ -58,14 +58,14 @@ __device__ __forceinline__ uint64_t spread6(uint64_t x) {
 }
 
 // Spreads the low 3 bits of x so that bit i lands on bit 3i.
-__device__ __forceinline__ uint32_t spread3_3(uint32_t x) {
+__host__ __device__ __forceinline__ uint32_t spread3_3(uint32_t x) {
     return (x & 1u) | ((x & 2u) << 2) | ((x & 4u) << 4);
 }
 
 // First 64 bits of the string whose level L (from the top) holds bit 31-L of
 // c[0], c[1], ..., c[5] in that order (Aila with c[3..5] = q(d) >> 3, and Two
 // Point with c[3..5] = q(p)).
-__device__ __forceinline__ uint64_t interleave6_64(const uint32_t c[6]) {
+__host__ __device__ __forceinline__ uint64_t interleave6_64(const uint32_t c[6]) {
     uint64_t hi = 0;
 #pragma unroll
     for (int s = 0; s < 6; ++s) hi |= spread6(c[s] >> 22) << (5 - s);  // levels 0..9
@@ -76,7 +76,7 @@ __device__ __forceinline__ uint64_t interleave6_64(const uint32_t c[6]) {
 
 // The compact string: levels 0..2 carry only c[0..2] (the always-zero
 // direction slots of the Aila string are dropped), later levels all six.
-__device__ __forceinline__ uint64_t interleave_compact_64(const uint32_t c[6]) {
+__host__ __device__ __forceinline__ uint64_t interleave_compact_64(const uint32_t c[6]) {
     uint32_t head = (spread3_3(c[0] >> 29) << 2) | (spread3_3(c[1] >> 29) << 1) |
                     spread3_3(c[2] >> 29);  // 9 bits, levels 0..2
     uint64_t body = 0;
@@ -190,10 +190,48 @@ __device__ __forceinline__ uint32_t div_floor_u64(unsigned long long sum, unsign
     return (uint32_t)q;
 }
 
-// 20-bit compacted Aila code: the length-table cell (Section 3.1.6).
-__device__ __forceinline__ uint32_t table_cell(const uint32_t qo[3], const uint32_t qd[3]) {
-    uint32_t c[6] = {qo[0], qo[1], qo[2], qd[0] >> 3, qd[1] >> 3, qd[2] >> 3};
-    return (uint32_t)(interleave_compact_64(c) >> 44);
+// 20-bit compacted Aila code: the length-table cell (Section 3.1.6).  The
+// first 20 bits of the compact string are o(12) d(3) o(3) d(2): levels 0..3
+// of the origin, then the first direction level (bit 31 of each quantised
+// direction, since the Aila direction is q >> 3), level 4 of the origin and
+// the second direction level of x and y.
+__host__ __device__ __forceinline__ uint32_t spread3_4(uint32_t x) {
+    return (x & 1u) | ((x & 2u) << 2) | ((x & 4u) << 4) | ((x & 8u) << 6);
+}
+__host__ __device__ __forceinline__ uint32_t table_cell(const uint32_t qo[3], const uint32_t qd[3]) {
+    const uint32_t o12 = (spread3_4(qo[0] >> 28) << 2) | (spread3_4(qo[1] >> 28) << 1) | spread3_4(qo[2] >> 28);
+    const uint32_t d3 = ((qd[0] >> 31) << 2) | ((qd[1] >> 31) << 1) | (qd[2] >> 31);
+    const uint32_t o3 = (((qo[0] >> 27) & 1u) << 2) | (((qo[1] >> 27) & 1u) << 1) | ((qo[2] >> 27) & 1u);
+    const uint32_t d2 = (((qd[0] >> 30) & 1u) << 1) | ((qd[1] >> 30) & 1u);
+    return (o12 << 8) | (d3 << 5) | (o3 << 2) | d2;
+}
+
+// Six-component interleave from a 64-entry table of 6-bit spreads (bit i of
+// the index at bit 6i, values below 2^31), as interleave6_64 computes it: the
+// first 30 bits of the string are levels 0..4 (bits 31..27 of every
+// component), the next 34 bits levels 5..10 (bits 26..21) without the last
+// two slots of level 10.
+__host__ __device__ __forceinline__ uint32_t spread6_small(uint32_t x) {
+    uint32_t r = 0;
+    for (int i = 0; i < 6; ++i) r |= ((x >> i) & 1u) << (6 * i);
+    return r;
+}
+__host__ __device__ __forceinline__ uint64_t interleave6_64_lut(const uint32_t c[6], const uint32_t *lut) {
+    uint32_t P = 0;
+    for (int s = 0; s < 6; ++s) P |= lut[c[s] >> 27] << (5 - s);
+    uint32_t B[6];
+    for (int s = 0; s < 6; ++s) B[s] = lut[(c[s] >> 21) & 63u];
+    const uint32_t lo = (B[0] << 3) | (B[1] << 2) | (B[2] << 1) | B[3] | (B[4] >> 1) | (B[5] >> 2);
+    const uint32_t hi = (P << 2) | ((B[0] >> 30) << 1) | (B[1] >> 30);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+// The table in shared memory, filled by the first 64 threads.  Call from
+// every thread of the block.
+__device__ __forceinline__ const uint32_t *block_spread6_lut() {
+    __shared__ uint32_t s_lut[64];
+    if (threadIdx.x < 64) s_lut[threadIdx.x] = spread6_small(threadIdx.x);
+    return s_lut;
 }
 
 }  // namespace rr

@@ -26,7 +26,7 @@ struct KeyArgs {
 // table: the ADAPTIVE cells.
 template <int LAYOUT, int TSRC>
 __device__ __forceinline__ uint64_t ray_key(const QuantFrame &f, float4 o, float4 d, uint32_t bits, float ratio,
-                                            float t_given, const ulonglong2 *table) {
+                                            float t_given, const ulonglong2 *table, const uint32_t *lut) {
     uint32_t qo[3], qd[3];
     float dh[3];
     quantise_ray(f, o, d, qo, qd, dh);
@@ -55,10 +55,10 @@ __device__ __forceinline__ uint64_t ray_key(const QuantFrame &f, float4 o, float
         c[3] = quantise_coord(f, 0, __fadd_rn(o.x, __fmul_rn(dh[0], t)));
         c[4] = quantise_coord(f, 1, __fadd_rn(o.y, __fmul_rn(dh[1], t)));
         c[5] = quantise_coord(f, 2, __fadd_rn(o.z, __fmul_rn(dh[2], t)));
-        key64 = interleave6_64(c);
+        key64 = interleave6_64_lut(c, lut);
     } else if (LAYOUT == RR_KEY_AILA || LAYOUT == RR_KEY_AILA_COMPACT) {
         uint32_t c[6] = {qo[0], qo[1], qo[2], qd[0] >> 3, qd[1] >> 3, qd[2] >> 3};
-        key64 = LAYOUT == RR_KEY_AILA ? interleave6_64(c) : interleave_compact_64(c);
+        key64 = LAYOUT == RR_KEY_AILA ? interleave6_64_lut(c, lut) : interleave_compact_64(c);
     } else if (LAYOUT == RR_KEY_ORIGIN) {
         key64 = morton3_64(qo[0], qo[1], qo[2]);
     } else if (LAYOUT == RR_KEY_REIS || LAYOUT == RR_KEY_COSTA) {
@@ -81,12 +81,13 @@ __device__ __forceinline__ uint64_t ray_key(const QuantFrame &f, float4 o, float
 // One ray per thread: two 16-byte loads, quantisation, interleave, one store.
 template <int LAYOUT, int TSRC, typename KeyT>
 __global__ void __launch_bounds__(256) key_kernel(KeyArgs a) {
-    const QuantFrame f = block_frame(a.lo, a.hi);
+    const uint32_t *lut = block_spread6_lut();
+    const QuantFrame f = block_frame(a.lo, a.hi);  // also publishes the table
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const float4 o = __ldg(a.o_tmin + i), d = __ldg(a.d_tmax + i);
     const float tg = TSRC == RR_T_GIVEN ? __ldg(a.t_given + i) : 0.0f;
-    static_cast<KeyT *>(a.keys)[i] = (KeyT)ray_key<LAYOUT, TSRC>(f, o, d, a.bits, a.ratio, tg, a.table);
+    static_cast<KeyT *>(a.keys)[i] = (KeyT)ray_key<LAYOUT, TSRC>(f, o, d, a.bits, a.ratio, tg, a.table, lut);
 }
 
 // Batches: the key of ray i in the frame (and table) of its segment, with the
@@ -98,6 +99,7 @@ __global__ void __launch_bounds__(256) key_batch_kernel(const BatchScene *__rest
                                                         const float4 *__restrict__ d_tmax, uint32_t n,
                                                         uint32_t bits, float ratio, KeyT *__restrict__ keys) {
     __shared__ uint32_t s_off[kMaxBatchSegments + 1];
+    const uint32_t *lut = block_spread6_lut();
     for (uint32_t k = threadIdx.x; k <= n_segs; k += blockDim.x) s_off[k] = seg_offsets[k];
     __syncthreads();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -112,7 +114,8 @@ __global__ void __launch_bounds__(256) key_batch_kernel(const BatchScene *__rest
     }
     const QuantFrame f = segs[lo].frame;
     const ulonglong2 *table = reinterpret_cast<const ulonglong2 *>(segs[lo].table);
-    const uint64_t k = ray_key<LAYOUT, TSRC>(f, __ldg(o_tmin + i), __ldg(d_tmax + i), bits, ratio, 0.0f, table);
+    const uint64_t k =
+        ray_key<LAYOUT, TSRC>(f, __ldg(o_tmin + i), __ldg(d_tmax + i), bits, ratio, 0.0f, table, lut);
     keys[i] = (KeyT)(((uint64_t)lo << bits) | k);
 }
 

@@ -48,7 +48,8 @@ EXPORTS = [
     "rr_pipeline_destroy", "rr_pipeline_run", "rr_pipeline_run_host", "rr_device_error",
     "rr_status_string", "rr_last_error_message", "rr_kernel_launch_count", "rr_sort_noalloc",
     "rr_coherence_capsule", "rr_trace_ex", "rr_sort_segments", "rr_batch_create", "rr_batch_destroy",
-    "rr_batch_info", "rr_batch_run", "rr_batch_run_loop", "rr_batch_tune",
+    "rr_batch_info", "rr_batch_run", "rr_batch_run_loop", "rr_batch_tune", "rr_server_create",
+    "rr_server_add_scene", "rr_server_submit", "rr_server_wait", "rr_server_stats", "rr_server_destroy",
 ]
 
 
@@ -74,6 +75,22 @@ class BatchConfig(C.Structure):
 
     def as_tuple(self):
         return (int(self.key_bits), int(self.radix_bits), int(self.trace_block))
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("budget_bytes", C.c_uint64), ("slots", C.c_uint32), ("max_batch_rays", C.c_uint32),
+                ("layout", C.c_uint32), ("t_source", C.c_uint32), ("ratio", C.c_float),
+                ("key_bits", C.c_uint32), ("radix_bits", C.c_uint32), ("trace_block", C.c_uint32)]
+
+
+class RequestTimes(C.Structure):
+    _fields_ = [("submit_ns", C.c_uint64), ("start_ns", C.c_uint64), ("done_ns", C.c_uint64),
+                ("batch_requests", C.c_uint32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("batches", C.c_uint64), ("max_batch_requests", C.c_uint64),
+                ("peak_reserved_bytes", C.c_uint64), ("reserved_bytes", C.c_uint64), ("waiting", C.c_uint64)]
 
 
 class BvhInfo(C.Structure):
@@ -121,6 +138,13 @@ def lib():
             L.rr_batch_run.argtypes = [vp, vp, vp, vp, vp, C.POINTER(BatchConfig), vp]
             L.rr_batch_run_loop.argtypes = [vp, vp, vp, vp, vp, C.POINTER(BatchConfig), vp]
             L.rr_batch_tune.argtypes = [vp, vp, vp, vp, C.POINTER(BatchConfig), C.POINTER(C.c_float), vp]
+            L.rr_server_create.argtypes = [C.POINTER(ServerConfig), C.POINTER(vp)]
+            L.rr_server_add_scene.argtypes = [vp, vp, vp, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                              C.POINTER(u32)]
+            L.rr_server_submit.argtypes = [vp, u32, vp, vp, u32, vp, C.POINTER(C.c_uint64)]
+            L.rr_server_wait.argtypes = [vp, C.c_uint64, C.c_double, C.POINTER(RequestTimes)]
+            L.rr_server_stats.argtypes = [vp, C.POINTER(ServerStats)]
+            L.rr_server_destroy.argtypes = [vp]
             L.rr_coherence_capsule.argtypes = [vp, vp, vp, u32, u32, C.c_float, vp, vp]
             L.rr_device_error.argtypes = [C.POINTER(C.c_uint32)]
             L.rr_status_string.argtypes = [i32]
@@ -444,6 +468,77 @@ class Batch:
         if getattr(self, "handle", None):
             lib().rr_batch_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- serving
+
+class Server:
+    """Owner of an rr_server: resident scenes, continuous batching of requests.
+
+    Host buffers passed to submit (numpy arrays or pinned CPU tensors) must stay
+    alive and untouched until wait() returns for the ticket."""
+
+    def __init__(self, budget_bytes: int, slots: int = 4, max_batch_rays: int = 1 << 24,
+                 layout: int = RR_KEY_TWO_POINT, t_source: int = RR_T_FIXED, ratio: float = 0.25,
+                 key_bits: int = 24, radix_bits: int = 8, trace_block: int = 128):
+        cfg = ServerConfig(int(budget_bytes), slots, max_batch_rays, layout, t_source, float(np.float32(ratio)),
+                           key_bits, radix_bits, trace_block)
+        h = C.c_void_p()
+        _check(lib().rr_server_create(C.byref(cfg), C.byref(h)), "rr_server_create")
+        self.handle = h
+        self._keep = []
+        self._held = {}
+
+    def add_scene(self, bvh: "BVH", aabb_lo, aabb_hi, table: "LengthTable" = None) -> int:
+        lo = (C.c_float * 3)(*[float(x) for x in aabb_lo])
+        hi = (C.c_float * 3)(*[float(x) for x in aabb_hi])
+        sid = C.c_uint32()
+        _check(lib().rr_server_add_scene(self.handle, bvh.handle, table.handle if table is not None else None,
+                                         lo, hi, C.byref(sid)), "rr_server_add_scene")
+        self._keep.append((bvh, table))
+        return sid.value
+
+    @staticmethod
+    def _host_ptr(a):
+        if isinstance(a, np.ndarray):
+            if not a.flags.c_contiguous:
+                raise ValueError("expected a contiguous array")
+            return a.ctypes.data
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError("expected a contiguous host tensor")
+        return a.data_ptr()
+
+    def submit(self, scene: int, o_tmin, d_tmax, hits_out, n: int | None = None) -> int:
+        n = int(o_tmin.shape[0]) if n is None else n
+        t = C.c_uint64()
+        _check(lib().rr_server_submit(self.handle, scene, self._host_ptr(o_tmin), self._host_ptr(d_tmax), n,
+                                      self._host_ptr(hits_out), C.byref(t)), "rr_server_submit")
+        self._held[t.value] = (o_tmin, d_tmax, hits_out)
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = 120.0) -> dict:
+        tm = RequestTimes()
+        _check(lib().rr_server_wait(self.handle, ticket, timeout_s, C.byref(tm)), "rr_server_wait")
+        self._held.pop(ticket, None)
+        return dict(submit_ns=tm.submit_ns, start_ns=tm.start_ns, done_ns=tm.done_ns,
+                    batch_requests=tm.batch_requests)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().rr_server_stats(self.handle, C.byref(st)), "rr_server_stats")
+        return {k: int(getattr(st, k)) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rr_server_destroy(self.handle)
+            self.handle = None
+            self._held.clear()
 
     def __del__(self):
         try:

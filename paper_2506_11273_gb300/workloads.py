@@ -403,3 +403,26 @@ def shadow_rays(tris: np.ndarray, n: int, seed: int, light_center=None, light_fr
     perm = rng.permutation(n)
     return make_rays(pts[perm].astype(np.float32), d[perm].astype(np.float32), np.float32(tmin),
                      np.float32(1.0 - 1e-4), perm.astype(np.uint32))
+
+
+def request_rays(tris: np.ndarray, n: int, kind: str, seed: int, eye=(0.5, 0.6, 0.1),
+                 tmin: float = 1e-4) -> Rays:
+    """Secondary rays of one serving request: origins uniform by area, in random
+    order.  ``kind`` "diffuse": cosine-weighted about the normal facing ``eye``;
+    "glossy": the Phong-100 lobe about the mirror direction of the ray from
+    ``eye`` (samples below the surface are folded back to the mirror direction)."""
+    rng = rng_for(seed * 31 + (7 if kind == "glossy" else 3))
+    pts, ids, _ = surface_points(tris, n, rng)
+    incoming = _normalize(pts - np.asarray(eye, np.float64)[None, :])
+    nn = tri_geometry(tris[ids])[3]
+    flip = np.sum(nn * incoming, axis=1) > 0
+    nn[flip] = -nn[flip]
+    if kind == "glossy":
+        r = _normalize(incoming - 2.0 * np.sum(incoming * nn, axis=1, keepdims=True) * nn)
+        d = _phong_dirs(r, PHONG_EXPONENT, rng)
+        below = np.sum(d * nn, axis=1) <= 0
+        d[below] = r[below]
+    else:
+        d = _cosine_dirs(nn, rng)
+    return make_rays(pts.astype(np.float32), d.astype(np.float32), np.float32(tmin),
+                     np.float32(np.inf), np.arange(n, dtype=np.uint32))
