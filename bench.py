@@ -44,7 +44,10 @@ BYTES_TRACE = 32 + 16
 BYTES_ACCUM = 32 + 16
 TRACE_PROFILE = os.path.join("profiles", "trace_kernel_config2_bounce3.md")
 TRACE_SOURCES = ["paper_2506_11273_gb300/csrc/rr_trace.cu", "paper_2506_11273_gb300/csrc/rr_trace.h",
-                 "paper_2506_11273_gb300/csrc/rr_common.cuh", "paper_2506_11273_gb300/csrc/rr_bvh.cpp"]
+                 "paper_2506_11273_gb300/csrc/rr_common.cuh", "paper_2506_11273_gb300/csrc/rr_bvh.cpp",
+                 "paper_2506_11273_gb300/csrc/rr_keymath.cuh", "paper_2506_11273_gb300/csrc/rr_batch.cuh"]
+# issue-slot peak: 4 warp instructions per cycle per SM (one per scheduler) x 152 SMs
+SMS, ISSUE_PER_SM_CYCLE, MAX_SM_MHZ = 152, 4, 2070.0
 
 
 def parse():
@@ -59,6 +62,23 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-execution measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     return ap.parse_args()
+
+
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over the ranks of the process group (x itself without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mrays(world: int, rays_per_rank_step: int, steps: int, max_total_ms: float) -> float:
+    """Weak scaling: every rank traces its own wavefront; the job's throughput is
+    all ranks' rays over the slowest rank's time."""
+    return world * rays_per_rank_step * steps / (max_total_ms * 1e-3) / 1e6
 
 
 def dist_env():
@@ -77,9 +97,10 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def measured_trace_traffic():
-    """DRAM bytes per trace launch from the committed ncu summary, or None when
-    the trace kernel's sources have changed since that capture."""
+def measured_trace_counts():
+    """(DRAM bytes, warp instructions) per trace launch from the committed ncu
+    summary, or (None, None) when the trace kernel's sources have changed since
+    that capture."""
     try:
         text = open(os.path.join(ROOT, TRACE_PROFILE)).read()
         h = hashlib.sha256()
@@ -87,12 +108,13 @@ def measured_trace_traffic():
             with open(os.path.join(ROOT, src), "rb") as f:
                 h.update(f.read())
     except OSError:
-        return None
+        return None, None
     m_bytes = re.search(r"traffic_bytes = (\d+)", text)
+    m_inst = re.search(r"inst_executed = (\d+)", text)
     m_hash = re.search(r"traffic_source_sha256_16: ([0-9a-f]+)", text)
-    if not m_bytes or not m_hash or h.hexdigest()[:16] != m_hash.group(1):
-        return None
-    return int(m_bytes.group(1))
+    if not m_bytes or not m_inst or not m_hash or h.hexdigest()[:16] != m_hash.group(1):
+        return None, None
+    return int(m_bytes.group(1)), int(m_inst.group(1))
 
 
 class ClockSampler:
@@ -290,12 +312,9 @@ def run_ours(args):
     launches = (rr.rr_kernel_launch_count() - l0)
     launches_timed = launches * args.steps // (args.steps + args.warmup)
     clocks = clk.summary()
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dev)
     ms_per_step = total_ms / args.steps
-    value = world * n * args.steps / (total_ms * 1e-3) / 1e6
+    value = whole_job_mrays(world, n, args.steps, total_ms)
     ph = np.array(ph)
     phase_ms = dict(zip(["key", "sort", "gather", "trace_and_accum", "spare"], [float(x) for x in np.median(ph, axis=0)]))
     phase_ms.pop("spare")
@@ -307,41 +326,42 @@ def run_ours(args):
     # unsorted trace of the same rays, same conditions
     tot_u, _, _ = timed(make_unsorted(B), args.steps, args.warmup)
     unsorted = n * args.steps / (tot_u * 1e-3) / 1e6
-    # the origin-direction (Aila) key on the same rays
-    step_aila, phases_aila = make_step(B, params_aila, False)
-    tot_a, _, ph_a = timed(step_aila, max(3, args.steps // 2), 3, phases_aila)
-    aila = n * max(3, args.steps // 2) / (tot_a * 1e-3) / 1e6
-    extra["aila_mrays"] = round(aila, 2)
-    extra["aila_trace_ms"] = round(float(np.median(np.array(ph_a)[:, 3])), 4)
-    # the paper's 32-bit Two Point key (Table 1 uses 32-bit keys) on the same rays
-    params_tp32 = rr.key_params(rr.RR_KEY_TWO_POINT, 32, lo, hi, t_source=rr.RR_T_ADAPTIVE, table=table)
-    step_32, phases_32 = make_step(B, params_tp32, False, bits=32)
-    tot_32, _, ph_32 = timed(step_32, max(3, args.steps // 2), 3, phases_32)
-    extra["two_point_32bit_mrays"] = round(n * max(3, args.steps // 2) / (tot_32 * 1e-3) / 1e6, 2)
-    extra["two_point_32bit_phases_ms"] = {k: round(float(v), 4) for k, v in
-                                          zip(["key", "sort", "gather", "trace"], np.median(np.array(ph_32), axis=0)[:4])}
+    if not args.no_extra:
+        # the origin-direction (Aila) key on the same rays
+        step_aila, phases_aila = make_step(B, params_aila, False)
+        tot_a, _, ph_a = timed(step_aila, max(3, args.steps // 2), 3, phases_aila)
+        aila = n * max(3, args.steps // 2) / (tot_a * 1e-3) / 1e6
+        extra["aila_mrays"] = round(aila, 2)
+        extra["aila_trace_ms"] = round(float(np.median(np.array(ph_a)[:, 3])), 4)
+        # the paper's 32-bit Two Point key (Table 1 uses 32-bit keys) on the same rays
+        params_tp32 = rr.key_params(rr.RR_KEY_TWO_POINT, 32, lo, hi, t_source=rr.RR_T_ADAPTIVE, table=table)
+        step_32, phases_32 = make_step(B, params_tp32, False, bits=32)
+        tot_32, _, ph_32 = timed(step_32, max(3, args.steps // 2), 3, phases_32)
+        extra["two_point_32bit_mrays"] = round(n * max(3, args.steps // 2) / (tot_32 * 1e-3) / 1e6, 2)
+        extra["two_point_32bit_phases_ms"] = {k: round(float(v), 4) for k, v in
+                                              zip(["key", "sort", "gather", "trace"], np.median(np.array(ph_32), axis=0)[:4])}
 
-    # cheaper reorderings of the same bounce (local sort, indirect access)
-    variants = {}
-    kv = max(3, args.steps // 2)
-    for name, kw in [("global64_indirect", dict(params=params_tp, accumulate=True, reorder="indirect")),
-                     ("global32_indirect", dict(params=params_tp32, accumulate=True, bits=32, reorder="indirect")),
-                     ("local1024_indirect", dict(params=params_tp, accumulate=True, sort="segment", segment=1024,
-                                                 reorder="indirect")),
-                     ("local2048_indirect", dict(params=params_tp, accumulate=True, sort="segment", segment=2048,
-                                                 reorder="indirect")),
-                     ("local4096_indirect", dict(params=params_tp, accumulate=True, sort="segment", segment=4096,
-                                                 reorder="indirect")),
-                     ("local4096_gather", dict(params=params_tp, accumulate=True, sort="segment", segment=4096))]:
-        st_v, pf_v = make_step(B, **kw)
-        tot_v, _, ph_v = timed(st_v, kv, 3, pf_v)
-        med = np.median(np.array(ph_v), axis=0)
-        variants[name] = {"mrays": round(n * kv / (tot_v * 1e-3) / 1e6, 2),
-                          "phases_ms": {k: round(float(v), 4) for k, v in
-                                        zip(["key", "sort", "gather", "trace"], med[:4])}}
-    extra["reorder_variants"] = variants
-    if rr.rr_device_error() != 0:
-        raise RuntimeError("device error flag set during the reorder variants")
+        # cheaper reorderings of the same bounce (local sort, indirect access)
+        variants = {}
+        kv = max(3, args.steps // 2)
+        for name, kw in [("global64_indirect", dict(params=params_tp, accumulate=True, reorder="indirect")),
+                         ("global32_indirect", dict(params=params_tp32, accumulate=True, bits=32, reorder="indirect")),
+                         ("local1024_indirect", dict(params=params_tp, accumulate=True, sort="segment", segment=1024,
+                                                     reorder="indirect")),
+                         ("local2048_indirect", dict(params=params_tp, accumulate=True, sort="segment", segment=2048,
+                                                     reorder="indirect")),
+                         ("local4096_indirect", dict(params=params_tp, accumulate=True, sort="segment", segment=4096,
+                                                     reorder="indirect")),
+                         ("local4096_gather", dict(params=params_tp, accumulate=True, sort="segment", segment=4096))]:
+            st_v, pf_v = make_step(B, **kw)
+            tot_v, _, ph_v = timed(st_v, kv, 3, pf_v)
+            med = np.median(np.array(ph_v), axis=0)
+            variants[name] = {"mrays": round(n * kv / (tot_v * 1e-3) / 1e6, 2),
+                              "phases_ms": {k: round(float(v), 4) for k, v in
+                                            zip(["key", "sort", "gather", "trace"], med[:4])}}
+        extra["reorder_variants"] = variants
+        if rr.rr_device_error() != 0:
+            raise RuntimeError("device error flag set during the reorder variants")
 
     if not args.no_extra:
         per_bounce = []
@@ -382,6 +402,21 @@ def run_ours(args):
 
     hbm, peak_kind = peaks()
     trace_ach = BYTES_TRACE * n / (phase_ms["trace"] * 1e-3) / 1e9
+    traffic, inst = (None, None) if args.small else measured_trace_counts()
+    sm_mhz = clocks.get("sm_mhz") or MAX_SM_MHZ
+    issue_peak = SMS * ISSUE_PER_SM_CYCLE * sm_mhz * 1e6 / 1e9  # G warp-instructions/s
+    if inst is not None:
+        # the trace kernel is bound by instruction issue (see its ncu summary)
+        ach = inst / (phase_ms["trace"] * 1e-3) / 1e9
+        roofline = {"bound": "alu", "kernel": "trace (fused trace + length-table update)",
+                    "achieved": round(ach, 1), "peak": round(issue_peak, 1),
+                    "unit": "G warp-instructions/s", "frac": round(ach / issue_peak, 4), "traffic": traffic,
+                    "work_per_launch": inst, "work_unit": "warp instructions (ncu smsp__inst_executed.sum)",
+                    "peak_kind": "derived: 4 issue slots x 152 SMs x sampled SM clock %.0f MHz" % sm_mhz}
+    else:
+        roofline = {"bound": "hbm", "kernel": "trace", "achieved": round(trace_ach, 1), "peak": hbm,
+                    "unit": "GB/s", "frac": round(trace_ach / hbm, 4), "traffic": None,
+                    "peak_kind": peak_kind, "algorithmic_bytes_per_ray": BYTES_TRACE}
     sort_ach = BYTES_SORT * n / (phase_ms["sort"] * 1e-3) / 1e9
     gather_ach = BYTES_GATHER * n / (phase_ms["gather"] * 1e-3) / 1e9
     key_ach = BYTES_KEY * n / (phase_ms["key"] * 1e-3) / 1e9
@@ -400,10 +435,10 @@ def run_ours(args):
         "unsorted_mrays": round(unsorted, 2),
         "speedup_vs_unsorted": round(value / unsorted, 3),
         "phases_ms": {k: round(v, 4) for k, v in phase_ms.items()},
-        "roofline": {"bound": "hbm", "kernel": "trace", "achieved": round(trace_ach, 1), "peak": hbm,
-                     "unit": "GB/s", "frac": round(trace_ach / hbm, 4),
-                     "traffic": None if args.small else measured_trace_traffic(),
-                     "peak_kind": peak_kind, "algorithmic_bytes_per_ray": BYTES_TRACE},
+        "roofline": roofline,
+        "trace_hbm": {"achieved": round(trace_ach, 1), "peak": hbm, "unit": "GB/s",
+                      "frac": round(trace_ach / hbm, 4), "algorithmic_bytes_per_ray": BYTES_TRACE,
+                      "peak_kind": peak_kind},
         "phase_roofline": {
             "key": {"gbs": round(key_ach, 1), "frac": round(key_ach / hbm, 3), "bytes_per_ray": BYTES_KEY},
             "sort": {"gbs": round(sort_ach, 1), "frac": round(sort_ach / hbm, 3), "bytes_per_ray": BYTES_SORT,

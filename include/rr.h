@@ -260,7 +260,7 @@ rr_status rr_trace_accumulate(const rr_bvh *bvh, const float *o_tmin, const floa
  * order (device, n uint32, or NULL): indirect access.  Work position k traces
  * ray order[k] and writes its hit to hits_out[order[k]], so a permutation from
  * rr_sort sets which rays share a warp without the rays being gathered first,
- * and the hits come back in the order of the input rays (Section 5, the
+ * and the hits come back in the order of the input rays (Section 4.4.1, the
  * indirect ray access of the CUDA trace kernel).  order must be a permutation
  * of [0, n): an entry >= n is skipped and sets RR_DEVERR_BAD_INDEX; a repeated
  * entry traces that ray twice.  NULL: position k traces ray k (rr_trace).
@@ -357,7 +357,7 @@ rr_status rr_coherence_capsule(const float *o_tmin, const float *d_tmax, const f
  * wavefront number above the key's bits (so every wavefront is sorted on its
  * own and stays in its range: the local sort of Section 3.2 with
  * wavefront-sized segments), and one trace of all rays through the
- * permutation (indirect access, Section 5), hits in input order.  The chain
+ * permutation (indirect access, Section 4.4.1), hits in input order.  The chain
  * is captured once per configuration and buffer set into a CUDA graph and
  * replayed (rr_batch_run); rr_batch_run_loop issues the same work wavefront
  * by wavefront through the single-wavefront calls, with the same results.

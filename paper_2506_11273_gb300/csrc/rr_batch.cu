@@ -4,7 +4,7 @@
 // stable sort of keys that carry the wavefront number above the key's own
 // bits, so each wavefront comes out sorted in place (Section 3.2's local
 // sort with wavefront-sized segments); the trace reads the rays through the
-// permutation (Section 5's indirect access) and writes hits in input order.
+// permutation (the indirect access of Section 4.4.1) and writes hits in input order.
 // A small autotuner times candidate (key bits, radix width, trace block)
 // configurations on the batch itself.
 #include <algorithm>

@@ -12,7 +12,7 @@
 //
 // Two variants serve the reordering study: indirect access (the queue hands
 // out positions of an index buffer, so sorted rays are traced without being
-// gathered first, Section 5) and any-hit traversal for shadow rays (the first
+// gathered first, Section 4.4.1) and any-hit traversal for shadow rays (the first
 // triangle found inside the interval ends the ray, Section 4).
 #include <chrono>
 #include <cmath>

@@ -1,4 +1,4 @@
-"""GPU parity of the cheaper reorderings (Section 3.2 local sort, Section 5
+"""GPU parity of the cheaper reorderings (Section 3.2 local sort, Section 4.4.1
 indirect ray access) and of the any-hit kernel for shadow rays (Section 4).
 
 Local sort: the permutation must equal the oracle's segment-wise stable sort bit
