@@ -307,8 +307,16 @@ __device__ __forceinline__ void accumulate_hit(unsigned long long *table, const 
 
 // MULTI: rays of several scenes in one launch (a batch); each lane finds the
 // segment of its ray and traces that segment's BVH (and updates its table).
+// Resident blocks asked of the compiler: 40 warps per SM (48 registers) for
+// the single-scene kernels; 32 warps for the fused table update and the batch
+// kernels, which would spill registers at 40.
+template <bool WIDE_STATE, int BLOCK>
+constexpr int trace_min_blocks() {
+    return (WIDE_STATE ? 1024 : 1280) / BLOCK > 0 ? (WIDE_STATE ? 1024 : 1280) / BLOCK : 1;
+}
+
 template <bool ACCUM, bool ANY, bool MULTI, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) trace_kernel(TraceArgs a) {
+__global__ void __launch_bounds__(BLOCK, (trace_min_blocks<ACCUM || MULTI, BLOCK>())) trace_kernel(TraceArgs a) {
     __shared__ uint32_t s_off[MULTI ? kMaxBatchSegments + 1 : 1];
     const uint32_t lane = threadIdx.x & 31u;
     uint2 stack[kTraceStack];
