@@ -513,6 +513,16 @@ rr_status rr_server_destroy(rr_server *srv);
 
 /* ---------------------------------------------------------------- diagnostics */
 
+/*
+ * rr_selftest_lookback_timeout - failure-detection self-test (no paper
+ * counterpart): runs one radix-sort pass over two tiles of which only the
+ * second is launched, so its look-back waits on a word nothing publishes until
+ * the bounded wait gives up (about 2^20 polls).  Afterwards rr_device_error
+ * reports RR_DEVERR_LOOKBACK_TIMEOUT and the device stays usable.  Allocates
+ * and frees its own buffers; synchronising.
+ */
+rr_status rr_selftest_lookback_timeout(void *stream);
+
 /* Reads and clears the current device's error word (RR_DEVERR_* flags); synchronising. */
 rr_status rr_device_error(uint32_t *flags_out);
 const char *rr_status_string(rr_status s);

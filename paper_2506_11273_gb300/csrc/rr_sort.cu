@@ -587,6 +587,61 @@ extern "C" rr_status rr_sort_segments(const void *keys_in, void *keys_out, uint3
     return RR_OK;
 }
 
+// ------------------------------------------------------------------ failure detection self-test
+//
+// One digit pass over two tiles of which only the second is launched: its
+// look-back waits for the first tile's word, which nothing publishes, until
+// the bounded spin gives up and records RR_DEVERR_LOOKBACK_TIMEOUT.  Without
+// its predecessor's counts the tile scatters below its true offsets, which
+// stay inside the output (all keys are zero: digit 0, positions 0..tile-1).
+
+extern "C" rr_status rr_selftest_lookback_timeout(void *stream) {
+    rr_status st;
+    DeviceState *ds = device_state(&st);
+    if (!ds) return st;
+    using K = uint32_t;
+    constexpr uint32_t tile = kSortBlock * SortTile<K>::kItems;
+    const uint32_t n = 2 * tile;
+    const SortPlan pl = plan_sort(n, 8, 8);
+    unsigned char *ws = nullptr;
+    K *keys = nullptr, *keys_out = nullptr;
+    uint32_t *perm = nullptr;
+    cudaError_t e = cudaMalloc(&ws, pl.total);
+    if (e == cudaSuccess) e = cudaMalloc(&keys, sizeof(K) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&keys_out, sizeof(K) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&perm, sizeof(uint32_t) * n);
+    cudaStream_t s = as_stream(stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, pl.total, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(keys, 0, sizeof(K) * n, s);
+    const uint32_t one = 1u;  // the tile counter hands the only block tile 1
+    uint32_t *counter = reinterpret_cast<uint32_t *>(ws + pl.off_counters);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(counter, &one, sizeof(one), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        PassArgs<K> a;
+        a.keys_in = keys;
+        a.vals_in = nullptr;
+        a.keys_out = keys_out;
+        a.vals_out = perm;
+        a.n = n;
+        a.shift = 0;
+        a.mask = 0xFFu;
+        a.hist = reinterpret_cast<const uint32_t *>(ws + pl.off_hist);
+        a.lookback = reinterpret_cast<unsigned long long *>(ws + pl.off_lookback);
+        a.tile_counter = counter;
+        a.err = ds->err;
+        onesweep_kernel<K, 8><<<1, kSortBlock, pass_smem<K, 8>(), s>>>(a);
+        note_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(ws);
+    cudaFree(keys);
+    cudaFree(keys_out);
+    cudaFree(perm);
+    if (e != cudaSuccess) return fail_cuda(e, "rr_selftest_lookback_timeout");
+    return RR_OK;
+}
+
 // ------------------------------------------------------------------ sort without allocation
 //
 // rr_sort_noalloc: the same sort with its scratch in a file-scope device array

@@ -50,6 +50,7 @@ EXPORTS = [
     "rr_coherence_capsule", "rr_trace_ex", "rr_sort_segments", "rr_batch_create", "rr_batch_destroy",
     "rr_batch_info", "rr_batch_run", "rr_batch_run_loop", "rr_batch_tune", "rr_server_create",
     "rr_server_add_scene", "rr_server_submit", "rr_server_wait", "rr_server_stats", "rr_server_destroy",
+    "rr_selftest_lookback_timeout",
 ]
 
 
@@ -145,6 +146,7 @@ def lib():
             L.rr_server_wait.argtypes = [vp, C.c_uint64, C.c_double, C.POINTER(RequestTimes)]
             L.rr_server_stats.argtypes = [vp, C.POINTER(ServerStats)]
             L.rr_server_destroy.argtypes = [vp]
+            L.rr_selftest_lookback_timeout.argtypes = [vp]
             L.rr_coherence_capsule.argtypes = [vp, vp, vp, u32, u32, C.c_float, vp, vp]
             L.rr_device_error.argtypes = [C.POINTER(C.c_uint32)]
             L.rr_status_string.argtypes = [i32]
@@ -563,6 +565,11 @@ def rr_coherence_capsule(o_tmin, d_tmax, hits, E: float, subset: int = 64, areas
 
 
 # ---------------------------------------------------------------- diagnostics
+
+def rr_selftest_lookback_timeout(stream=None):
+    """Runs the look-back wait out on purpose (bounded); see include/rr.h."""
+    _check(lib().rr_selftest_lookback_timeout(_stream(stream)), "rr_selftest_lookback_timeout")
+
 
 def rr_device_error() -> int:
     v = C.c_uint32()
