@@ -70,7 +70,7 @@ def compare(tris, o_tmin, d_tmax, gpu_hits, or_hits, or_info, max_ambiguous=None
                                                       _cos(d, tris, gt) < GRAZING_COS or
                                                       _near_interval_end(g_plane[1], tmin, tmax)))
         (ambiguous if amb else definite).append(int(i))
-    res = dict(n=n, ties=ties, ambiguous=len(ambiguous), definite=len(definite),
+    res = dict(n=n, ties=ties, ambiguous=len(ambiguous), definite=len(definite), ambiguous_idx=ambiguous,
                hit_rate=float(np.mean(o_tri != oracle.MISS)) if n else 0.0,
                examples=[(i, float(gpu_hits[i, 0]), int(g_tri[i]), float(o_t[i]), int(o_tri[i]),
                           float(or_info[i, 1]), o_tmin[i].tolist(), d_tmax[i].tolist())
