@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the per-bounce and e2e sweeps")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-execution measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--sweep", action="store_true",
+                    help="scale sweep instead of the bench line: 4.67M-triangle scene, 3840x2160 bounce-2 "
+                         "wavefront, key bits 16/32/48/64 x radix 4/8, phase split")
     return ap.parse_args()
 
 
@@ -469,6 +472,116 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- scale sweep
+
+def run_sweep(args):
+    """Key bits 16/32/48/64 x radix width 4/8 on the 4,674,304-triangle scene and
+    its 3840x2160 bounce-2 wavefront (Two Point key, adaptive estimate): the
+    phase split key / sort / gather / trace (+ table update) and MRays/s."""
+    import torch
+
+    from paper_2506_11273_gb300 import rr
+    from paper_2506_11273_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    if args.small:
+        tris = W.scene_terrain(seed=3, cells_x=128, cells_z=256, n_boxes=1000)
+        cam = W.Camera(width=960, height=540)
+    else:
+        tris = W.scene_terrain(seed=3, cells_x=1024, cells_z=2048, n_boxes=40000)
+        cam = W.Camera(width=3840, height=2160)
+    lo, hi = W.scene_aabb(tris)
+    bvh = rr.BVH(tris)
+    table = rr.LengthTable(lo, hi)
+    rays = W.camera_rays(cam, seed=3)
+    o, d, _ = rr.to_device_rays(rays, dev)
+    h = torch.empty(len(rays), 4, device=dev)
+    rr.rr_trace(bvh, o, d, h)
+    table.accumulate(o, d, h)
+    rays = W.next_bounce(tris, rays, h.cpu().numpy(), 1, seed=3)
+    del o, d, h
+    n = len(rays)
+    o, d, p = rr.to_device_rays(rays, dev)
+    so, sd, sp = torch.empty_like(o), torch.empty_like(d), torch.empty_like(p)
+    hits = torch.empty(n, 4, device=dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    setup_s = time.time() - t0
+
+    def timed(fn, K, W_=3):
+        evs = None
+        for _ in range(W_):
+            flush.zero_()
+            fn(None)
+        torch.cuda.synchronize()
+        rows = []
+        for _ in range(K):
+            flush.zero_()
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            fn(evs)
+            torch.cuda.synchronize()
+            rows.append([evs[i].elapsed_time(evs[i + 1]) for i in range(4)])
+        return np.median(np.array(rows), axis=0)
+
+    def unsorted(evs):
+        if evs:
+            for e in evs[:4]:
+                e.record(stream)
+        rr.rr_trace(bvh, o, d, hits)
+        if evs:
+            evs[4].record(stream)
+
+    t_uns = float(timed(unsorted, 5)[3])
+    rows = []
+    for bits in (16, 32, 48, 64):
+        keys = torch.empty(n, dtype=rr.key_dtype(bits), device=dev)
+        params = rr.key_params(rr.RR_KEY_TWO_POINT, bits, lo, hi, t_source=rr.RR_T_ADAPTIVE, table=table)
+        for radix in (4, 8):
+            ws = rr.sort_workspace(n, bits, radix, dev)
+
+            def step(evs):
+                if evs:
+                    evs[0].record(stream)
+                rr.rr_compute_keys(o, d, params, keys)
+                if evs:
+                    evs[1].record(stream)
+                rr.rr_sort(keys, None, perm, n, bits, radix, ws)
+                if evs:
+                    evs[2].record(stream)
+                rr.rr_permute(o, d, p, perm, so, sd, sp)
+                if evs:
+                    evs[3].record(stream)
+                rr.rr_trace_accumulate(bvh, so, sd, hits, table)
+                if evs:
+                    evs[4].record(stream)
+
+            ph = timed(step, 5)
+            kb = 8 if bits > 32 else 4
+            passes = -(-bits // radix)
+            sort_bytes = n * (kb + passes * 2 * (kb + 4) - 4)
+            hbm, _ = peaks()
+            rows.append({"key_bits": bits, "radix_bits": radix,
+                         "key_ms": round(float(ph[0]), 4), "sort_ms": round(float(ph[1]), 4),
+                         "gather_ms": round(float(ph[2]), 4), "trace_accum_ms": round(float(ph[3]), 4),
+                         "sorted_e2e_mrays": round(n / (float(ph.sum()) * 1e-3) / 1e6, 1),
+                         "sort_gbs": round(sort_bytes / (float(ph[1]) * 1e-3) / 1e9, 1),
+                         "sort_frac_hbm": round(sort_bytes / (float(ph[1]) * 1e-3) / 1e9 / hbm, 3)})
+            del ws
+        del keys
+    if rr.rr_device_error() != 0:
+        raise RuntimeError("device error flag set during the sweep")
+    out = {"metric": METRIC, "sweep": rows, "unit": UNIT,
+           "config": {"workload": "scale sweep: %d-triangle terrain, %dx%d bounce-2 wavefront (%d rays); Two Point "
+                                  "key (adaptive estimate)" % (tris.shape[0], cam.width, cam.height, n),
+                      "l2": "flushed between steps (256 MB write)"},
+           "unsorted_trace_ms": round(t_uns, 4), "unsorted_mrays": round(n / (t_uns * 1e-3) / 1e6, 1),
+           "setup_s": round(setup_s, 1)}
+    print(json.dumps(out), flush=True)
+
+
 # ----------------------------------------------------------------------------- batched
 
 # 4 resident scenes of ~50k, 250k, 1M and 2M triangles built like the path-tracer
@@ -733,6 +846,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_ours(args)
 
