@@ -308,28 +308,29 @@ __device__ __forceinline__ void accumulate_hit(unsigned long long *table, const 
 // MULTI: rays of several scenes in one launch (a batch); each lane finds the
 // segment of its ray and traces that segment's BVH (and updates its table).
 // Resident blocks asked of the compiler: 40 warps per SM (48 registers) for
-// the single-scene kernels; 32 warps for the fused table update and the batch
-// kernels, which would spill registers at 40.
+// the single-scene kernels; 32 warps for the batch kernels, whose per-lane
+// scene pointers would spill registers at 40.
 template <bool WIDE_STATE, int BLOCK>
 constexpr int trace_min_blocks() {
     return (WIDE_STATE ? 1024 : 1280) / BLOCK > 0 ? (WIDE_STATE ? 1024 : 1280) / BLOCK : 1;
 }
 
 template <bool ACCUM, bool ANY, bool MULTI, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, (trace_min_blocks<ACCUM || MULTI, BLOCK>())) trace_kernel(TraceArgs a) {
+__global__ void __launch_bounds__(BLOCK, (trace_min_blocks<MULTI, BLOCK>())) trace_kernel(TraceArgs a) {
     __shared__ uint32_t s_off[MULTI ? kMaxBatchSegments + 1 : 1];
     const uint32_t lane = threadIdx.x & 31u;
+    // the table's quantisation frame is the same for the whole launch: it lives
+    // in shared memory, not in every thread's registers during traversal
+    __shared__ QuantFrame s_frame;
+    __shared__ float s_invE;
     uint2 stack[kTraceStack];
-    QuantFrame f0;
-    float invE0 = 0.0f;
-    if (ACCUM && !MULTI) {
-        f0 = make_frame(a.tlo, a.thi);
-        invE0 = __fdiv_rn(1.0f, f0.E);
+    if (ACCUM && !MULTI && threadIdx.x == 0) {
+        s_frame = make_frame(a.tlo, a.thi);
+        s_invE = __fdiv_rn(1.0f, s_frame.E);
     }
-    if (MULTI) {
+    if (MULTI)
         for (uint32_t k = threadIdx.x; k <= a.n_segs; k += BLOCK) s_off[k] = a.seg_offsets[k];
-        __syncthreads();
-    }
+    if (MULTI || ACCUM) __syncthreads();
     while (true) {
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(a.queue, kQueueBatch);
@@ -345,9 +346,7 @@ __global__ void __launch_bounds__(BLOCK, (trace_min_blocks<ACCUM || MULTI, BLOCK
                 continue;
             }
             SceneRef sc = a.scene;
-            unsigned long long *table = a.table;
-            QuantFrame f = f0;
-            float invE = invE0;
+            uint32_t seg = 0;
             if (MULTI) {
                 // the last segment starting at or before i (empty segments share
                 // their start with the next one, which wins)
@@ -364,11 +363,7 @@ __global__ void __launch_bounds__(BLOCK, (trace_min_blocks<ACCUM || MULTI, BLOCK
                 sc.tris = bs->tris;
                 sc.planes = bs->planes;
                 sc.n_nodes = bs->n_nodes;
-                if (ACCUM) {
-                    table = bs->table;
-                    f = bs->frame;
-                    invE = bs->invE;
-                }
+                seg = lo;
             }
             RayState r;
             const float4 o = __ldg(a.o_tmin + i), d = __ldg(a.d_tmax + i);
@@ -390,7 +385,14 @@ __global__ void __launch_bounds__(BLOCK, (trace_min_blocks<ACCUM || MULTI, BLOCK
             }
             const float4 h = ray_result(r, sc);
             a.hits[i] = h;
-            if (ACCUM && table) accumulate_hit(table, f, invE, o, d, h);
+            if (ACCUM) {
+                if (MULTI) {  // the segment's table and frame, read once the ray is done
+                    const BatchScene *bs = a.segs + seg;
+                    if (bs->table) accumulate_hit(bs->table, bs->frame, bs->invE, o, d, h);
+                } else if (a.table) {
+                    accumulate_hit(a.table, s_frame, s_invE, o, d, h);
+                }
+            }
         }
     }
     __syncthreads();
