@@ -344,6 +344,16 @@ def run_ours(args):
         extra["two_point_32bit_phases_ms"] = {k: round(float(v), 4) for k, v in
                                               zip(["key", "sort", "gather", "trace"], np.median(np.array(ph_32), axis=0)[:4])}
 
+        # Two Point Real (the paper's bound): the estimate is each ray's true hit
+        # distance, taken from the unsorted trace above
+        tg = (B["hits"][:, 0] * torch.linalg.norm(B["d"][:, :3], dim=1)).contiguous()
+        params_real = rr.key_params(rr.RR_KEY_TWO_POINT, KEY_BITS, lo, hi, t_source=rr.RR_T_GIVEN, t_given=tg)
+        step_real, phases_real = make_step(B, params_real, False)
+        tot_r, _, ph_r = timed(step_real, max(3, args.steps // 2), 3, phases_real)
+        extra["two_point_real_mrays"] = round(n * max(3, args.steps // 2) / (tot_r * 1e-3) / 1e6, 2)
+        extra["two_point_real_trace_ms"] = round(float(np.median(np.array(ph_r)[:, 3])), 4)
+        extra["shadow_rays"] = bench_shadow(args, B, bvh, tris, lo, hi, flush, timed, stream)
+
         # cheaper reorderings of the same bounce (local sort, indirect access)
         variants = {}
         kv = max(3, args.steps // 2)
@@ -470,6 +480,74 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- shadow rays
+
+def bench_shadow(args, B, bvh, tris, lo, hi, flush, timed, stream):
+    """Next-event shadow rays from the hit points of the bounce-3 wavefront (in
+    wavefront order) to a square light of side 0.05 E above the scene (the
+    paper's evaluation setup, Section 4), traced with the any-hit kernel:
+    unsorted versus sorted by the Octahedron, Aila and Two Point keys (32 bits;
+    Two Point with the known distance to the light as its estimate)."""
+    import torch
+
+    from paper_2506_11273_gb300 import rr
+    from paper_2506_11273_gb300 import workloads as W
+
+    h = B["hits"].cpu().numpy()  # unsorted hits, wavefront order
+    o = B["o"].cpu().numpy()
+    d = B["d"].cpu().numpy()
+    hit = np.ascontiguousarray(h[:, 3]).view(np.uint32) != rr.MISS
+    pts = o[hit, :3].astype(np.float64) + h[hit, 0:1].astype(np.float64) * d[hit, :3].astype(np.float64)
+    E = float(np.max(hi - lo))
+    center = ((lo[0] + hi[0]) / 2, hi[1] + 0.05 * E, (lo[2] + hi[2]) / 2)
+    sr = W.shadow_rays_to_light(pts, center, 0.05 * E, seed=5)
+    n = len(sr)
+    so, sd, _ = rr.to_device_rays(sr, B["o"].device)
+    hits = torch.empty(n, 4, device=so.device)
+    perm = torch.empty(n, dtype=torch.int32, device=so.device)
+    keys = torch.empty(n, dtype=torch.int32, device=so.device)
+    go, gd = torch.empty_like(so), torch.empty_like(sd)
+    ws = rr.sort_workspace(n, 32, RADIX_BITS, so.device)
+    t_light = torch.linalg.norm(sd[:, :3], dim=1).contiguous()  # p = o + d^ |d| is the light point
+
+    def unsorted():
+        rr.rr_trace_ex(bvh, so, sd, hits, flags=rr.RR_TRACE_ANY_HIT)
+
+    def variant(params):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+
+        def step():
+            ev[0].record(stream)
+            rr.rr_compute_keys(so, sd, params, keys)
+            ev[1].record(stream)
+            rr.rr_sort(keys, None, perm, n, 32, RADIX_BITS, ws)
+            ev[2].record(stream)
+            rr.rr_permute(so, sd, None, perm, go, gd, None)
+            ev[3].record(stream)
+            rr.rr_trace_ex(bvh, go, gd, hits, flags=rr.RR_TRACE_ANY_HIT)
+            ev[4].record(stream)
+
+        return step, lambda: [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
+
+    K = max(3, args.steps // 2)
+    tot_u, _, _ = timed(unsorted, K, 3)
+    occluded = float(np.mean(np.ascontiguousarray(hits.cpu().numpy()[:, 3]).view(np.uint32) != rr.MISS))
+    out = {"rays": n, "occluded_fraction": round(occluded, 3), "unsorted_mrays": round(n * K / (tot_u * 1e-3) / 1e6, 1)}
+    for name, params in [("octahedron32", rr.key_params(rr.RR_KEY_OCTAHEDRON, 32, lo, hi)),
+                         ("aila32", rr.key_params(rr.RR_KEY_AILA, 32, lo, hi)),
+                         ("two_point32_light", rr.key_params(rr.RR_KEY_TWO_POINT, 32, lo, hi,
+                                                             t_source=rr.RR_T_GIVEN, t_given=t_light))]:
+        st, pf = variant(params)
+        tot, _, ph = timed(st, K, 3, pf)
+        med = np.median(np.array(ph), axis=0)
+        out[name] = {"sorted_e2e_mrays": round(n * K / (tot * 1e-3) / 1e6, 1),
+                     "trace_mrays": round(n / (float(med[3]) * 1e-3) / 1e6, 1),
+                     "phases_ms": {k: round(float(v), 4) for k, v in zip(["key", "sort", "gather", "trace"], med)}}
+    if rr.rr_device_error() != 0:
+        raise RuntimeError("device error flag set during the shadow-ray measurement")
+    return out
 
 
 # ----------------------------------------------------------------------------- scale sweep

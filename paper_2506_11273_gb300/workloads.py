@@ -426,3 +426,17 @@ def request_rays(tris: np.ndarray, n: int, kind: str, seed: int, eye=(0.5, 0.6, 
         d = _cosine_dirs(nn, rng)
     return make_rays(pts.astype(np.float32), d.astype(np.float32), np.float32(tmin),
                      np.float32(np.inf), np.arange(n, dtype=np.uint32))
+
+
+def shadow_rays_to_light(points: np.ndarray, center, side: float, seed: int, tmin: float = 1e-4) -> Rays:
+    """Shadow rays from given surface points (e.g. a wavefront's hit points, in
+    their order) to uniform points of a square area light of side ``side``
+    centred at ``center`` (horizontal, as in ``shadow_rays``); d = light point -
+    origin, t in (tmin, 1 - 1e-4)."""
+    rng = rng_for(seed * 17 + 9)
+    n = points.shape[0]
+    c = np.asarray(center, np.float64)
+    lp = c[None, :] + np.stack([(rng.random(n) - 0.5) * side, np.zeros(n), (rng.random(n) - 0.5) * side], axis=1)
+    d = lp - points.astype(np.float64)
+    return make_rays(points.astype(np.float32), d.astype(np.float32), np.float32(tmin), np.float32(1.0 - 1e-4),
+                     np.arange(n, dtype=np.uint32))
