@@ -305,19 +305,49 @@ __device__ __forceinline__ void accumulate_hit(unsigned long long *table, const 
     atomicAdd(table + 2 * (size_t)cell + 1, 1ull);
 }
 
-// MULTI: rays of several scenes in one launch (a batch); each lane finds the
-// segment of its ray and traces that segment's BVH (and updates its table).
-// Resident blocks asked of the compiler: 40 warps per SM (48 registers) for
-// the single-scene kernels; 32 warps for the batch kernels, whose per-lane
-// scene pointers would spill registers at 40.
-template <bool WIDE_STATE, int BLOCK>
-constexpr int trace_min_blocks() {
-    return (WIDE_STATE ? 1024 : 1280) / BLOCK > 0 ? (WIDE_STATE ? 1024 : 1280) / BLOCK : 1;
+// Traces ray i against the scene `sc` and writes its hit: the traversal loop
+// shared by every kernel variant.
+template <bool ANY>
+__device__ __forceinline__ float4 trace_ray(const SceneRef &sc, uint2 *stack, uint32_t *err, float4 o, float4 d) {
+    RayState r;
+    ray_begin(r, sc, o, d);
+    while (true) {
+        if (r.g_hits != 0u && !ray_visit_node(r, stack, sc)) {
+            atomicOr(err, RR_DEVERR_TRACE_STACK);
+            r.best_tri = kMiss;
+            break;
+        }
+        ray_test_triangles<ANY>(r, sc);
+        if (r.g_hits == 0u) {
+            if (r.sp == 0) break;
+            const uint2 e = stack[--r.sp];
+            r.g_base = e.x;
+            r.g_hits = e.y & 0xFFu;
+            r.g_imask = (e.y >> 8) & 0xFFu;
+        }
+    }
+    return ray_result(r, sc);
 }
 
+// Resident blocks asked of the compiler: 40 warps per SM (48 registers).
+template <int BLOCK>
+constexpr int trace_min_blocks() {
+    return 1280 / BLOCK > 0 ? 1280 / BLOCK : 1;
+}
+
+// Dynamic shared memory of the batch kernels: the scene of every segment, then
+// the segment offsets.
+inline size_t multi_smem(uint32_t n_segs) { return sizeof(SceneRef) * n_segs + sizeof(uint32_t) * (n_segs + 1); }
+
+// MULTI: rays of several scenes in one launch (a batch); each lane finds the
+// segment of its ray and traces that segment's BVH (and updates its table).
+// The segments' scenes sit in shared memory, so a lane keeps only its segment
+// number in registers during traversal.
 template <bool ACCUM, bool ANY, bool MULTI, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, (trace_min_blocks<MULTI, BLOCK>())) trace_kernel(TraceArgs a) {
-    __shared__ uint32_t s_off[MULTI ? kMaxBatchSegments + 1 : 1];
+__global__ void __launch_bounds__(BLOCK, (trace_min_blocks<BLOCK>())) trace_kernel(TraceArgs a) {
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    SceneRef *s_sc = reinterpret_cast<SceneRef *>(s_dyn);
+    uint32_t *s_off = reinterpret_cast<uint32_t *>(s_sc + (MULTI ? a.n_segs : 0));
     const uint32_t lane = threadIdx.x & 31u;
     // the table's quantisation frame is the same for the whole launch: it lives
     // in shared memory, not in every thread's registers during traversal
@@ -328,8 +358,16 @@ __global__ void __launch_bounds__(BLOCK, (trace_min_blocks<MULTI, BLOCK>())) tra
         s_frame = make_frame(a.tlo, a.thi);
         s_invE = __fdiv_rn(1.0f, s_frame.E);
     }
-    if (MULTI)
+    if (MULTI) {
         for (uint32_t k = threadIdx.x; k <= a.n_segs; k += BLOCK) s_off[k] = a.seg_offsets[k];
+        for (uint32_t k = threadIdx.x; k < a.n_segs; k += BLOCK) {
+            const BatchScene *bs = a.segs + k;
+            s_sc[k].nodes = bs->nodes;
+            s_sc[k].tris = bs->tris;
+            s_sc[k].planes = bs->planes;
+            s_sc[k].n_nodes = bs->n_nodes;
+        }
+    }
     if (MULTI || ACCUM) __syncthreads();
     while (true) {
         uint32_t base = 0;
@@ -345,7 +383,8 @@ __global__ void __launch_bounds__(BLOCK, (trace_min_blocks<MULTI, BLOCK>())) tra
                 atomicOr(a.err, RR_DEVERR_BAD_INDEX);
                 continue;
             }
-            SceneRef sc = a.scene;
+            const float4 o = __ldg(a.o_tmin + i), d = __ldg(a.d_tmax + i);
+            float4 h;
             uint32_t seg = 0;
             if (MULTI) {
                 // the last segment starting at or before i (empty segments share
@@ -358,32 +397,11 @@ __global__ void __launch_bounds__(BLOCK, (trace_min_blocks<MULTI, BLOCK>())) tra
                     else
                         hi = mid;
                 }
-                const BatchScene *bs = a.segs + lo;
-                sc.nodes = bs->nodes;
-                sc.tris = bs->tris;
-                sc.planes = bs->planes;
-                sc.n_nodes = bs->n_nodes;
                 seg = lo;
+                h = trace_ray<ANY>(s_sc[seg], stack, a.err, o, d);
+            } else {
+                h = trace_ray<ANY>(a.scene, stack, a.err, o, d);
             }
-            RayState r;
-            const float4 o = __ldg(a.o_tmin + i), d = __ldg(a.d_tmax + i);
-            ray_begin(r, sc, o, d);
-            while (true) {
-                if (r.g_hits != 0u && !ray_visit_node(r, stack, sc)) {
-                    atomicOr(a.err, RR_DEVERR_TRACE_STACK);
-                    r.best_tri = kMiss;
-                    break;
-                }
-                ray_test_triangles<ANY>(r, sc);
-                if (r.g_hits == 0u) {
-                    if (r.sp == 0) break;
-                    const uint2 e = stack[--r.sp];
-                    r.g_base = e.x;
-                    r.g_hits = e.y & 0xFFu;
-                    r.g_imask = (e.y >> 8) & 0xFFu;
-                }
-            }
-            const float4 h = ray_result(r, sc);
             a.hits[i] = h;
             if (ACCUM) {
                 if (MULTI) {  // the segment's table and frame, read once the ray is done
@@ -487,23 +505,26 @@ extern "C" rr_status rr_bvh_get_info(const rr_bvh *b, rr_bvh_info *info) {
 namespace {
 
 template <bool ACC, bool ANY, bool MULTI, int BLOCK>
-int trace_blocks_per_sm() {
+int trace_blocks_per_sm(size_t smem) {
     static int bps = 0;
-    if (bps == 0) {
+    static size_t bps_smem = 0;
+    if (bps == 0 || bps_smem != smem) {  // the batch kernels' shared memory varies with the segments
         int v = 0;
         const cudaError_t e =
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, trace_kernel<ACC, ANY, MULTI, BLOCK>, BLOCK, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, trace_kernel<ACC, ANY, MULTI, BLOCK>, BLOCK, smem);
         bps = (e != cudaSuccess || v < 1) ? 1 : v;
+        bps_smem = smem;
     }
     return bps;
 }
 
 template <bool ACC, bool ANY, bool MULTI, int BLOCK>
 void trace_enqueue(const TraceArgs &a, int sm_count, cudaStream_t s) {
+    const size_t smem = MULTI ? multi_smem(a.n_segs) : 0;
     const uint32_t want = (a.n + kQueueBatch - 1) / kQueueBatch;  // warps that can get work
-    uint32_t grid = (uint32_t)sm_count * (uint32_t)trace_blocks_per_sm<ACC, ANY, MULTI, BLOCK>();
+    uint32_t grid = (uint32_t)sm_count * (uint32_t)trace_blocks_per_sm<ACC, ANY, MULTI, BLOCK>(smem);
     grid = std::max(1u, std::min(grid, (want + BLOCK / 32 - 1) / (BLOCK / 32)));
-    trace_kernel<ACC, ANY, MULTI, BLOCK><<<grid, BLOCK, 0, s>>>(a);
+    trace_kernel<ACC, ANY, MULTI, BLOCK><<<grid, BLOCK, smem, s>>>(a);
 }
 
 rr_status launch_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax, const uint32_t *order, uint32_t n,
