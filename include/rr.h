@@ -58,6 +58,7 @@ typedef enum {
 #define RR_DEVERR_LOOKBACK_TIMEOUT 0x1u
 #define RR_DEVERR_TRACE_STACK 0x2u
 #define RR_DEVERR_BAD_INDEX 0x4u /* an index buffer entry was >= n; that entry was skipped */
+#define RR_DEVERR_COPY_TIMEOUT 0x8u /* a bulk copy into shared memory did not complete in time */
 
 /* Sorting-key layouts (Section 3.1, Figure 2). */
 typedef enum {

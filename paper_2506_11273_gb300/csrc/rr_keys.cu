@@ -1,15 +1,18 @@
 // Sorting keys (Section 3.1, Figure 2) and the adaptive ray-length table
 // (Section 3.1.6).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
 #include "rr_batch.cuh"
 #include "rr_common.cuh"
 #include "rr_keymath.cuh"
+#include "rr_tma.cuh"
 
 namespace rr {
 
 struct KeyArgs {
+    uint32_t *err;  // device error word
     const float4 *o_tmin;
     const float4 *d_tmax;
     uint32_t n;
@@ -78,16 +81,60 @@ __device__ __forceinline__ uint64_t ray_key(const QuantFrame &f, float4 o, float
     return key64 >> (64 - bits);
 }
 
-// One ray per thread: two 16-byte loads, quantisation, interleave, one store.
+// Persistent blocks walk over tiles of 256 rays.  Each tile's origins and
+// directions arrive in shared memory by two bulk asynchronous copies completed
+// on an mbarrier, issued one tile ahead into the other of two buffers, so the
+// loads of the next tile overlap the key arithmetic of this one.  One ray per
+// thread per tile: quantisation, interleave, one store.
+constexpr int kKeyTile = 256;
+constexpr uint32_t kCopySpinLimit = 1u << 22;  // polls of a copy's barrier before giving up
+
 template <int LAYOUT, int TSRC, typename KeyT>
-__global__ void __launch_bounds__(256) key_kernel(KeyArgs a) {
+__global__ void __launch_bounds__(kKeyTile, 6) key_kernel(KeyArgs a) {
+    __shared__ __align__(128) float4 s_o[2][kKeyTile];
+    __shared__ __align__(128) float4 s_d[2][kKeyTile];
+    __shared__ __align__(8) uint64_t s_bar[2];
+    const uint32_t tid = threadIdx.x;
+    const uint32_t tiles = (a.n + kKeyTile - 1) / kKeyTile;
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        mbar_init_fence();
+    }
     const uint32_t *lut = block_spread6_lut();
-    const QuantFrame f = block_frame(a.lo, a.hi);  // also publishes the table
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    const float4 o = __ldg(a.o_tmin + i), d = __ldg(a.d_tmax + i);
-    const float tg = TSRC == RR_T_GIVEN ? __ldg(a.t_given + i) : 0.0f;
-    static_cast<KeyT *>(a.keys)[i] = (KeyT)ray_key<LAYOUT, TSRC>(f, o, d, a.bits, a.ratio, tg, a.table, lut);
+    const QuantFrame f = block_frame(a.lo, a.hi);  // synchronises: barriers and table published
+    auto issue = [&](uint32_t t, uint32_t buf) {
+        const uint32_t first = t * kKeyTile;
+        const uint32_t bytes = min((uint32_t)kKeyTile, a.n - first) * (uint32_t)sizeof(float4);
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&s_bar[buf], 2 * bytes);
+        bulk_copy_g2s(s_o[buf], a.o_tmin + first, bytes, &s_bar[buf]);
+        bulk_copy_g2s(s_d[buf], a.d_tmax + first, bytes, &s_bar[buf]);
+    };
+    if (tid == 0 && blockIdx.x < tiles) issue(blockIdx.x, 0);
+    uint32_t k = 0;
+    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x, ++k) {
+        const uint32_t buf = k & 1u, parity = (k >> 1) & 1u;
+        const uint32_t next = t + gridDim.x;
+        if (tid == 0 && next < tiles) issue(next, buf ^ 1u);
+        const bool ok = mbar_wait_bounded(&s_bar[buf], parity, kCopySpinLimit);
+        if (!__syncthreads_and(ok)) {
+            // give up on this launch; let the copy already issued for the
+            // next tile land before the block's shared memory goes away
+            if (tid == 0) {
+                atomicOr(a.err, RR_DEVERR_COPY_TIMEOUT);
+                if (next < tiles) mbar_wait_bounded(&s_bar[buf ^ 1u], ((k + 1) >> 1) & 1u, kCopySpinLimit);
+            }
+            break;
+        }
+        const uint32_t i = t * kKeyTile + tid;
+        if (i < a.n) {
+            const float tg = TSRC == RR_T_GIVEN ? __ldg(a.t_given + i) : 0.0f;
+            static_cast<KeyT *>(a.keys)[i] =
+                (KeyT)ray_key<LAYOUT, TSRC>(f, s_o[buf][tid], s_d[buf][tid], a.bits, a.ratio, tg, a.table, lut);
+        }
+        __syncthreads();  // every thread is done with `buf` before it is refilled
+    }
 }
 
 // Batches: the key of ray i in the frame (and table) of its segment, with the
@@ -127,13 +174,26 @@ __global__ void batch_frame_kernel(BatchScene *segs, const float *boxes, uint32_
     segs[k].invE = __fdiv_rn(1.0f, f.E);
 }
 
+template <typename F>
+static uint32_t persistent_grid(F kernel, uint32_t tiles, int sm_count) {
+    static int bps = 0;
+    if (bps == 0) {
+        int v = 0;
+        bps = (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, kKeyTile, 0) == cudaSuccess && v > 0) ? v : 1;
+    }
+    return std::max(1u, std::min(tiles, (uint32_t)(sm_count * bps)));
+}
+
 template <int LAYOUT, int TSRC>
-static void launch_keys(const KeyArgs &a, bool wide, cudaStream_t s) {
-    dim3 grid((a.n + 255) / 256);
-    if (wide)
-        key_kernel<LAYOUT, TSRC, unsigned long long><<<grid, 256, 0, s>>>(a);
-    else
-        key_kernel<LAYOUT, TSRC, uint32_t><<<grid, 256, 0, s>>>(a);
+static void launch_keys(const KeyArgs &a, bool wide, int sm_count, cudaStream_t s) {
+    const uint32_t tiles = (a.n + kKeyTile - 1) / kKeyTile;
+    if (wide) {
+        auto k = key_kernel<LAYOUT, TSRC, unsigned long long>;
+        k<<<persistent_grid(k, tiles, sm_count), kKeyTile, 0, s>>>(a);
+    } else {
+        auto k = key_kernel<LAYOUT, TSRC, uint32_t>;
+        k<<<persistent_grid(k, tiles, sm_count), kKeyTile, 0, s>>>(a);
+    }
 }
 
 __global__ void table_init_kernel(ulonglong2 *cells) {
@@ -280,27 +340,30 @@ extern "C" rr_status rr_compute_keys(const float *o_tmin, const float *d_tmax, u
     a.table = nullptr;
     a.keys = keys_out;
     rr_status st;
-    if (!device_state(&st)) return st;
+    DeviceState *ds = device_state(&st);
+    if (!ds) return st;
+    a.err = ds->err;
+    const int sms = ds->sm_count;
     cudaStream_t s = as_stream(stream);
     if (p->layout == RR_KEY_AILA) {
-        launch_keys<RR_KEY_AILA, 0>(a, wide, s);
+        launch_keys<RR_KEY_AILA, 0>(a, wide, sms, s);
     } else if (p->layout == RR_KEY_AILA_COMPACT) {
-        launch_keys<RR_KEY_AILA_COMPACT, 0>(a, wide, s);
+        launch_keys<RR_KEY_AILA_COMPACT, 0>(a, wide, sms, s);
     } else if (p->layout == RR_KEY_ORIGIN) {
-        launch_keys<RR_KEY_ORIGIN, 0>(a, wide, s);
+        launch_keys<RR_KEY_ORIGIN, 0>(a, wide, sms, s);
     } else if (p->layout == RR_KEY_REIS) {
-        launch_keys<RR_KEY_REIS, 0>(a, wide, s);
+        launch_keys<RR_KEY_REIS, 0>(a, wide, sms, s);
     } else if (p->layout == RR_KEY_COSTA) {
-        launch_keys<RR_KEY_COSTA, 0>(a, wide, s);
+        launch_keys<RR_KEY_COSTA, 0>(a, wide, sms, s);
     } else if (p->layout == RR_KEY_OCTAHEDRON) {
-        launch_keys<RR_KEY_OCTAHEDRON, 0>(a, wide, s);
+        launch_keys<RR_KEY_OCTAHEDRON, 0>(a, wide, sms, s);
     } else if (p->t_source == RR_T_FIXED) {
         if (!std::isfinite(p->ratio)) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: ratio not finite");
-        launch_keys<RR_KEY_TWO_POINT, RR_T_FIXED>(a, wide, s);
+        launch_keys<RR_KEY_TWO_POINT, RR_T_FIXED>(a, wide, sms, s);
     } else if (p->t_source == RR_T_GIVEN) {
         if (!p->t_given || !aligned(p->t_given, 4))
             return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: t_given missing or misaligned");
-        launch_keys<RR_KEY_TWO_POINT, RR_T_GIVEN>(a, wide, s);
+        launch_keys<RR_KEY_TWO_POINT, RR_T_GIVEN>(a, wide, sms, s);
     } else {
         const rr_length_table *t = p->table;
         if (!t) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: ADAPTIVE needs a table");
@@ -308,7 +371,7 @@ extern "C" rr_status rr_compute_keys(const float *o_tmin, const float *d_tmax, u
             std::memcmp(t->box.hi, p->aabb_hi, sizeof(float) * 3))
             return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: table was created for another box");
         a.table = reinterpret_cast<const ulonglong2 *>(t->cells);
-        launch_keys<RR_KEY_TWO_POINT, RR_T_ADAPTIVE>(a, wide, s);
+        launch_keys<RR_KEY_TWO_POINT, RR_T_ADAPTIVE>(a, wide, sms, s);
     }
     note_launches(1);
     return check_launch("rr_compute_keys");

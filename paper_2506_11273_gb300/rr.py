@@ -31,6 +31,7 @@ RR_T_FIXED, RR_T_ADAPTIVE, RR_T_GIVEN = 0, 1, 2
 RR_DEVERR_LOOKBACK_TIMEOUT = 0x1
 RR_DEVERR_TRACE_STACK = 0x2
 RR_DEVERR_BAD_INDEX = 0x4
+RR_DEVERR_COPY_TIMEOUT = 0x8
 RR_TRACE_ANY_HIT = 0x1
 MISS = 0xFFFFFFFF
 TABLE_CELLS = 1 << 20
