@@ -228,3 +228,33 @@ def test_batch_without_reordering(world):
     check_hits(world, h1.cpu().numpy(), h_or, i_or)
     assert rr.rr_device_error() == 0
     b.close()
+
+
+def test_batch_degenerate_shapes(world):
+    """One wavefront; wavefronts that are all empty but one; a batch with no rays."""
+    o, d = _dev(world["o"]), _dev(world["d"])
+    s = 0
+    lo, hi = world["boxes"][s]
+    f = world["fronts"][0]
+    n0 = len(f)
+    one = rr.Batch([(world["bvhs"][s], None, lo, hi, n0)], rr.RR_KEY_TWO_POINT)
+    assert one.info()["seg_bits"] == 0
+    h = torch.empty(n0, 4, device="cuda")
+    p = torch.empty(n0, dtype=torch.int32, device="cuda")
+    one.run(o[:n0].contiguous(), d[:n0].contiguous(), h, rr.Batch.config(32, 8, 256), p)
+    keys = oracle.compute_keys(oracle.TWO_POINT, 32, f.o_tmin, f.d_tmax, lo, hi)
+    assert np.array_equal(rr.u32_to_numpy(p), oracle.stable_sort(keys)[0])
+    one.close()
+    sparse = rr.Batch([(world["bvhs"][1], None, *world["boxes"][1], 0), (world["bvhs"][s], None, lo, hi, n0),
+                       (world["bvhs"][2], None, *world["boxes"][2], 0)], rr.RR_KEY_TWO_POINT)
+    h2 = torch.empty(n0, 4, device="cuda")
+    sparse.run(o[:n0].contiguous(), d[:n0].contiguous(), h2, rr.Batch.config(30, 8, 256), p)
+    assert np.array_equal(rr.u32_to_numpy(p), oracle.stable_sort(
+        oracle.compute_keys(oracle.TWO_POINT, 30, f.o_tmin, f.d_tmax, lo, hi))[0])
+    assert np.array_equal(_bits(h2.cpu().numpy()), _bits(h.cpu().numpy()))
+    sparse.close()
+    empty = rr.Batch([(world["bvhs"][s], None, lo, hi, 0)], rr.RR_KEY_AILA)
+    assert empty.n == 0
+    empty.run(o, d, h, rr.Batch.config(16, 8, 256))  # nothing to do
+    empty.close()
+    assert rr.rr_device_error() == 0

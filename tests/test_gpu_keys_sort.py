@@ -329,3 +329,28 @@ def test_adaptive_keys_with_extreme_table_contents(soup):
     k_or = oracle.compute_keys(oracle.TWO_POINT, 64, rays.o_tmin, rays.d_tmax, lo, hi, tsrc=oracle.T_ADAPTIVE,
                                table=ot)
     assert np.array_equal(k_gpu, k_or)
+
+
+@pytest.mark.parametrize("n", [1, 3, 255, 256, 257, 1000, 4097, 65535])
+@pytest.mark.parametrize("name,bits,tsrc", [("two_point", 64, "adaptive"), ("aila", 32, "fixed"),
+                                            ("octahedron", 40, "fixed"), ("two_point", 20, "given")])
+def test_keys_ragged_sizes(soup, soup_hits, n, name, bits, tsrc):
+    """Ray counts that end inside a 256-ray tile: the staged copies of the last
+    tile are shorter, and every key still matches the oracle."""
+    tris, rays, lo, hi = soup
+    sub = rays.subset(np.arange(n))
+    layout, olayout = LAYOUTS[name]
+    ts, ots = TSRC[tsrc]
+    E = oracle.largest_extent(lo, hi)
+    tab, ot, tg = None, None, None
+    if tsrc == "adaptive":
+        ot = oracle.LengthTable(E)
+        ot.accumulate(lo, hi, rays.o_tmin, rays.d_tmax, soup_hits)
+        tab = rr.LengthTable(lo, hi)
+        tab.write(ot.sum, ot.cnt)
+    if tsrc == "given":
+        tg = np.random.default_rng(n).random(n).astype(np.float32)
+    k_gpu = gpu_keys(sub, layout, bits, lo, hi, tsrc=ts, t_given=tg, table=tab)
+    k_or = oracle.compute_keys(olayout, bits, sub.o_tmin, sub.d_tmax, lo, hi, tsrc=ots, t_given=tg, table=ot)
+    assert np.array_equal(k_gpu, k_or)
+    assert_no_device_error()

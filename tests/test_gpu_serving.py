@@ -135,3 +135,17 @@ def test_server_rejects_bad_requests(scenes):
     t = srv.submit(1, big.o_tmin[:0], big.d_tmax[:0], h[:0])  # empty request
     srv.wait(t)
     srv.close()
+
+
+def test_server_closes_with_requests_in_flight(scenes):
+    """Closing the server finishes what was submitted and frees it, waited for or not."""
+    tris, bvhs, boxes, reqs = scenes
+    srv = _server(scenes, budget=64 << 20, slots=2)
+    hits = [np.zeros((r.o_tmin.shape[0], 4), np.float32) for _, r in reqs]
+    for (s, r), h in zip(reqs, hits):
+        srv.submit(s, r.o_tmin, r.d_tmax, h)
+    srv.close()  # no waits
+    for (s, r), h in zip(reqs[:3], hits[:3]):
+        oh, oi = oracle.BVH(tris[s]).trace(r.o_tmin, r.d_tmax)
+        compare(tris[s], r.o_tmin, r.d_tmax, h, oh, oi)
+    assert rr.rr_device_error() == 0
