@@ -314,6 +314,13 @@ def run_ours(args):
         total_ms, times, ph = timed(step_tp, args.steps, args.warmup, phases_tp)
     launches = (rr.rr_kernel_launch_count() - l0)
     launches_timed = launches * args.steps // (args.steps + args.warmup)
+    E_scene = float(np.max(hi - lo))
+
+    def capsule_mean(o_, d_, h_):
+        """Mean capsule area of the runs of 64 consecutive rays (Section 4.3)."""
+        return float(rr.rr_coherence_capsule(o_, d_, h_, E_scene).mean().item())
+
+    coherence = {"two_point_adaptive64": capsule_mean(B["so"], B["sd"], B["hits"])}
     clocks = clk.summary()
     total_ms = max_over_ranks(total_ms, dev)
     ms_per_step = total_ms / args.steps
@@ -329,6 +336,7 @@ def run_ours(args):
     # unsorted trace of the same rays, same conditions
     tot_u, _, _ = timed(make_unsorted(B), args.steps, args.warmup)
     unsorted = n * args.steps / (tot_u * 1e-3) / 1e6
+    coherence["unsorted"] = capsule_mean(B["o"], B["d"], B["hits"])
     if not args.no_extra:
         # the origin-direction (Aila) key on the same rays
         step_aila, phases_aila = make_step(B, params_aila, False)
@@ -336,6 +344,7 @@ def run_ours(args):
         aila = n * max(3, args.steps // 2) / (tot_a * 1e-3) / 1e6
         extra["aila_mrays"] = round(aila, 2)
         extra["aila_trace_ms"] = round(float(np.median(np.array(ph_a)[:, 3])), 4)
+        coherence["aila64"] = capsule_mean(B["so"], B["sd"], B["hits"])
         # the paper's 32-bit Two Point key (Table 1 uses 32-bit keys) on the same rays
         params_tp32 = rr.key_params(rr.RR_KEY_TWO_POINT, 32, lo, hi, t_source=rr.RR_T_ADAPTIVE, table=table)
         step_32, phases_32 = make_step(B, params_tp32, False, bits=32)
@@ -352,6 +361,7 @@ def run_ours(args):
         tot_r, _, ph_r = timed(step_real, max(3, args.steps // 2), 3, phases_real)
         extra["two_point_real_mrays"] = round(n * max(3, args.steps // 2) / (tot_r * 1e-3) / 1e6, 2)
         extra["two_point_real_trace_ms"] = round(float(np.median(np.array(ph_r)[:, 3])), 4)
+        coherence["two_point_real64"] = capsule_mean(B["so"], B["sd"], B["hits"])
         extra["shadow_rays"] = bench_shadow(args, B, bvh, tris, lo, hi, flush, timed, stream)
 
         # cheaper reorderings of the same bounce (local sort, indirect access)
@@ -467,6 +477,8 @@ def run_ours(args):
         "setup_s": round(setup_s, 1),
     }
     out.update(extra)
+    out["coherence_capsule_m64"] = {k: {"mean_area": round(v, 4), "relative_to_unsorted":
+                                        round(v / coherence["unsorted"], 3)} for k, v in coherence.items()}
     if not args.no_batched:
         out["batched"] = bench_batched(args, dev, flush)
     if not args.no_serving:
