@@ -404,7 +404,7 @@ rr_status rr_batch_info(const rr_batch *batch, uint32_t *n_rays, uint32_t *seg_b
 /*
  * rr_batch_run - the whole batch as one CUDA graph launch on `stream`.  The
  * graph for (cfg, o_tmin, d_tmax, hits_out, perm_out) is captured on first use
- * and kept with the batch.  hits_out (device, float4 per ray) in input order;
+ * and kept with the batch (at most 32 graphs; the oldest is dropped).  hits_out (device, float4 per ray) in input order;
  * perm_out (device, uint32 per ray, or NULL): the batch permutation, whose
  * range of wavefront k is the stable sort of that wavefront's keys (global
  * indices).  Runs of one batch must not overlap in time (they share the
@@ -479,7 +479,12 @@ typedef struct {
 
 typedef struct rr_server rr_server;
 
-/* Starts the worker thread; the current device is the server's. */
+/*
+ * Starts the worker thread; the current device is the server's.  Device memory
+ * of admitted groups comes from the device's default stream-ordered memory
+ * pool, whose release threshold the server raises to budget_bytes so that
+ * freed memory stays cached for the next groups.
+ */
 rr_status rr_server_create(const rr_server_config *cfg, rr_server **out);
 
 /*

@@ -19,6 +19,8 @@ using namespace rr;
 
 namespace {
 
+constexpr size_t kMaxGraphs = 32;  // captured graphs kept per batch
+
 struct GraphEntry {
     rr_batch_config cfg;
     const float *o, *d;
@@ -248,6 +250,10 @@ extern "C" rr_status rr_batch_run(rr_batch *b, const float *o_tmin, const float 
     for (GraphEntry &x : b->graphs)
         if (same_cfg(x.cfg, *cfg) && x.o == o_tmin && x.d == d_tmax && x.hits == hits_out && x.perm == perm) g = &x;
     if (!g) {
+        if (b->graphs.size() >= kMaxGraphs) {  // keep the cache bounded: drop the oldest graph
+            cudaGraphExecDestroy(b->graphs.front().exec);
+            b->graphs.erase(b->graphs.begin());
+        }
         // capture the chain once for these buffers and this configuration
         cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return fail_cuda(e, "rr_batch_run: begin capture");

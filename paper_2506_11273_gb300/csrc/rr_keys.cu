@@ -174,12 +174,16 @@ __global__ void batch_frame_kernel(BatchScene *segs, const float *boxes, uint32_
     segs[k].invE = __fdiv_rn(1.0f, f.E);
 }
 
-template <typename F>
-static uint32_t persistent_grid(F kernel, uint32_t tiles, int sm_count) {
+// Blocks of one key-kernel variant that fit on the device at once (its
+// occupancy is queried once per variant).
+template <int LAYOUT, int TSRC, typename KeyT>
+static uint32_t key_grid(uint32_t tiles, int sm_count) {
     static int bps = 0;
     if (bps == 0) {
         int v = 0;
-        bps = (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, kKeyTile, 0) == cudaSuccess && v > 0) ? v : 1;
+        const cudaError_t e =
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, key_kernel<LAYOUT, TSRC, KeyT>, kKeyTile, 0);
+        bps = (e == cudaSuccess && v > 0) ? v : 1;
     }
     return std::max(1u, std::min(tiles, (uint32_t)(sm_count * bps)));
 }
@@ -187,13 +191,11 @@ static uint32_t persistent_grid(F kernel, uint32_t tiles, int sm_count) {
 template <int LAYOUT, int TSRC>
 static void launch_keys(const KeyArgs &a, bool wide, int sm_count, cudaStream_t s) {
     const uint32_t tiles = (a.n + kKeyTile - 1) / kKeyTile;
-    if (wide) {
-        auto k = key_kernel<LAYOUT, TSRC, unsigned long long>;
-        k<<<persistent_grid(k, tiles, sm_count), kKeyTile, 0, s>>>(a);
-    } else {
-        auto k = key_kernel<LAYOUT, TSRC, uint32_t>;
-        k<<<persistent_grid(k, tiles, sm_count), kKeyTile, 0, s>>>(a);
-    }
+    if (wide)
+        key_kernel<LAYOUT, TSRC, unsigned long long>
+            <<<key_grid<LAYOUT, TSRC, unsigned long long>(tiles, sm_count), kKeyTile, 0, s>>>(a);
+    else
+        key_kernel<LAYOUT, TSRC, uint32_t><<<key_grid<LAYOUT, TSRC, uint32_t>(tiles, sm_count), kKeyTile, 0, s>>>(a);
 }
 
 __global__ void table_init_kernel(ulonglong2 *cells) {
