@@ -222,6 +222,10 @@ def test_pipeline_matches_oracle_config1(name, layout, olayout, bits, tsrc, otsr
             pipe.run_host(rays.o_tmin, rays.d_tmax, rays.payload, gh, gp)
         keys, perm, so, sd, sp, h, info = oracle_bounce(tris, rays, lo, hi, olayout, bits, otsrc, otable, obvh)
         assert np.array_equal(gp, sp)  # payload order == oracle permutation
+        if entry == "device":
+            dev_hits = gh.copy()
+        else:  # the host entry returns the device entry's hits, bit for bit
+            assert np.array_equal(gh.view(np.uint32), dev_hits.view(np.uint32))
         res = compare(tris, so, sd, gh, h, info)
         if adaptive:
             check_table_close(table, otable, res["ambiguous"])
