@@ -783,7 +783,7 @@ SERVE_POOL = 1 << 18    # distinct rays generated per scene and kind (requests t
 SERVE_MAX_REQ = 4 << 20
 
 
-def bench_serving(args, dev):
+def bench_serving(args, dev, slots: int = 4, max_batch_rays: int = 1 << 25, fractions=(0.25, 0.5, 0.75, 0.9)):
     """Poisson arrivals of requests of log-uniform 4k-4M rays (60% diffuse, 40%
     glossy) over 8 resident scenes, served with continuous batching under a
     120 GB budget; p50/p99 latency and throughput at several offered loads."""
@@ -798,8 +798,8 @@ def bench_serving(args, dev):
     scale = 0.05 if small else 1.0
     lo_n, hi_n = int(4096 * scale) + 1, int(SERVE_MAX_REQ * scale)
     pool_n = max(1024, int(SERVE_POOL * scale))
-    srv = rr.Server(budget_bytes=SERVE_BUDGET, slots=4, max_batch_rays=1 << 25, key_bits=24, radix_bits=8,
-                    trace_block=128)
+    srv = rr.Server(budget_bytes=SERVE_BUDGET, slots=slots, max_batch_rays=max(max_batch_rays, hi_n), key_bits=24,
+                    radix_bits=8, trace_block=256)
     scenes = []
     pools = {}
     t0 = time.time()
@@ -860,14 +860,15 @@ def bench_serving(args, dev):
     cap_mrays = max(run_load(1e6, 256 / 1e6, seed=s)["throughput_mrays"] for s in (1, 3))
     cap_rps = cap_mrays * 1e6 / mean_n
     loads = []
-    for frac in (0.25, 0.5, 0.75, 0.9):
+    for frac in fractions:
         loads.append(dict(run_load(frac * cap_rps, 1.5 if not small else 0.5, seed=int(frac * 100)),
                           load_frac=frac))
     st = srv.stats()
     srv.close()
     return {"workload": "Poisson arrivals of log-uniform %d-%d-ray requests (60%% diffuse, 40%% glossy) over 8 "
-                        "scenes of %s triangles; budget %d GB, 4 stream slots, Two Point key 24 bits" %
-                        (lo_n, hi_n, "/".join(str(n) for _, n in scenes), SERVE_BUDGET >> 30),
+                        "scenes of %s triangles; budget %d GB, %d stream slots, groups of at most %d rays, "
+                        "Two Point key 24 bits" % (lo_n, hi_n, "/".join(str(n) for _, n in scenes),
+                                                   SERVE_BUDGET >> 30, slots, max(max_batch_rays, hi_n)),
             "capacity_mrays": cap_mrays, "loads": loads, "setup_s": round(setup_s, 1),
             "batches": st["batches"], "max_batch_requests": st["max_batch_requests"],
             "peak_reserved_gb": round(st["peak_reserved_bytes"] / 2**30, 2)}
