@@ -783,10 +783,13 @@ SERVE_POOL = 1 << 18    # distinct rays generated per scene and kind (requests t
 SERVE_MAX_REQ = 4 << 20
 
 
-def bench_serving(args, dev, slots: int = 4, max_batch_rays: int = 1 << 25, fractions=(0.25, 0.5, 0.75, 0.9)):
+def bench_serving(args, dev, slots: int = 4, max_batch_rays: int = 1 << 23, fractions=(0.25, 0.5, 0.75, 0.9),
+                  reserve: int = 8 << 30):
     """Poisson arrivals of requests of log-uniform 4k-4M rays (60% diffuse, 40%
     glossy) over 8 resident scenes, served with continuous batching under a
-    120 GB budget; p50/p99 latency and throughput at several offered loads."""
+    120 GB budget; p50/p99 latency and throughput at several offered loads.
+    Groups are capped at 8M rays (smaller groups finish sooner, so requests that
+    share one wait less) and 8 GB of the memory pool is taken up front."""
     import threading
 
     import torch
@@ -799,7 +802,7 @@ def bench_serving(args, dev, slots: int = 4, max_batch_rays: int = 1 << 25, frac
     lo_n, hi_n = int(4096 * scale) + 1, int(SERVE_MAX_REQ * scale)
     pool_n = max(1024, int(SERVE_POOL * scale))
     srv = rr.Server(budget_bytes=SERVE_BUDGET, slots=slots, max_batch_rays=max(max_batch_rays, hi_n), key_bits=24,
-                    radix_bits=8, trace_block=256)
+                    radix_bits=8, trace_block=256, reserve_bytes=reserve)
     scenes = []
     pools = {}
     t0 = time.time()

@@ -307,6 +307,14 @@ extern "C" rr_status rr_server_create(const rr_server_config *cfg, rr_server **o
         uint64_t thr = cfg->budget_bytes;
         e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
+    if (e == cudaSuccess && cfg->reserve_bytes > 0) {
+        // grow the pool once now; freed memory stays cached up to the threshold
+        void *tmp = nullptr;
+        const size_t bytes = (size_t)std::min<uint64_t>(cfg->reserve_bytes, cfg->budget_bytes);
+        e = cudaMallocAsync(&tmp, bytes, s->slots[0].stream);
+        if (e == cudaSuccess) e = cudaFreeAsync(tmp, s->slots[0].stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->slots[0].stream);
+    }
     if (e != cudaSuccess) {
         for (Slot &sl : s->slots) {
             if (sl.stream) cudaStreamDestroy(sl.stream);

@@ -82,7 +82,8 @@ class BatchConfig(C.Structure):
 class ServerConfig(C.Structure):
     _fields_ = [("budget_bytes", C.c_uint64), ("slots", C.c_uint32), ("max_batch_rays", C.c_uint32),
                 ("layout", C.c_uint32), ("t_source", C.c_uint32), ("ratio", C.c_float),
-                ("key_bits", C.c_uint32), ("radix_bits", C.c_uint32), ("trace_block", C.c_uint32)]
+                ("key_bits", C.c_uint32), ("radix_bits", C.c_uint32), ("trace_block", C.c_uint32),
+                ("reserve_bytes", C.c_uint64)]
 
 
 class RequestTimes(C.Structure):
@@ -489,9 +490,9 @@ class Server:
 
     def __init__(self, budget_bytes: int, slots: int = 4, max_batch_rays: int = 1 << 24,
                  layout: int = RR_KEY_TWO_POINT, t_source: int = RR_T_FIXED, ratio: float = 0.25,
-                 key_bits: int = 24, radix_bits: int = 8, trace_block: int = 128):
+                 key_bits: int = 24, radix_bits: int = 8, trace_block: int = 256, reserve_bytes: int = 0):
         cfg = ServerConfig(int(budget_bytes), slots, max_batch_rays, layout, t_source, float(np.float32(ratio)),
-                           key_bits, radix_bits, trace_block)
+                           key_bits, radix_bits, trace_block, int(reserve_bytes))
         h = C.c_void_p()
         _check(lib().rr_server_create(C.byref(cfg), C.byref(h)), "rr_server_create")
         self.handle = h
