@@ -13,17 +13,30 @@
  *   rr_length_table_accumulate
  *                    the adaptive ray-length cache updated after each trace (Section 3.1.6)
  *
+ * and around it:
+ *
+ *   rr_trace_ex          indirect ray access through a permutation (Section 4.4.1)
+ *                        and any-hit traversal for shadow rays (Section 4)
+ *   rr_sort_segments     local (block-wise) sort (Section 3.2)
+ *   rr_coherence_capsule the capsule coherence measure (Section 4.3)
+ *   rr_pipeline_*        one bounce behind one handle
+ *   rr_batch_*           many wavefronts over resident scenes as one CUDA graph, with
+ *                        an autotuner
+ *   rr_server_*          a serving loop with continuous batching under a memory budget
+ *
  * Conventions shared by every call:
  *  - Device buffers are owned by the caller.  The library owns only the opaque
- *    handles (rr_bvh, rr_length_table, rr_pipeline) and the device memory behind them.
+ *    handles (rr_bvh, rr_length_table, rr_pipeline, rr_batch, rr_server) and the
+ *    device memory behind them.
  *  - Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy default
  *    stream) and the call returns without synchronising, unless stated otherwise.
  *  - Arguments are checked on the host before anything is enqueued.  A bad
  *    argument returns RR_ERR_INVALID_ARG and enqueues nothing.  n == 0 is a
  *    no-op that returns RR_OK.
- *  - Failures inside kernels (a radix-sort look-back that waited too long, a
- *    traversal stack overflow) never trap: the kernel records a flag in a
- *    per-device error word and finishes.  rr_device_error() reads and clears it.
+ *  - Failures inside kernels (a radix-sort look-back or a bulk copy that waited
+ *    too long, a traversal stack overflow, an index out of range) never trap:
+ *    the kernel records a flag in a per-device error word and finishes.
+ *    rr_device_error() reads and clears it.
  *  - Ray layout (structure of arrays, 16-byte aligned):
  *      o_tmin  float4 per ray: origin.x, origin.y, origin.z, tmin
  *      d_tmax  float4 per ray: direction.x, .y, .z, tmax
