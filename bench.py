@@ -364,10 +364,36 @@ def run_ours(args):
         coherence["two_point_real64"] = capsule_mean(B["so"], B["sd"], B["hits"])
         extra["shadow_rays"] = bench_shadow(args, B, bvh, tris, lo, hi, flush, timed, stream)
 
+        # every key family of Section 3.1 at 32 bits (the paper's Table 1 uses
+        # 32-bit keys): trace speedup over the unsorted rays and the capsule
+        # coherence of the sorted order
+        t_uns_ms = tot_u / args.steps
+        fam = {}
+        kf = max(3, args.steps // 2)
+        for name, layout, ts, kw in [
+                ("origin", rr.RR_KEY_ORIGIN, rr.RR_T_FIXED, {}), ("reis", rr.RR_KEY_REIS, rr.RR_T_FIXED, {}),
+                ("costa", rr.RR_KEY_COSTA, rr.RR_T_FIXED, {}), ("aila", rr.RR_KEY_AILA, rr.RR_T_FIXED, {}),
+                ("aila_compact", rr.RR_KEY_AILA_COMPACT, rr.RR_T_FIXED, {}),
+                ("octahedron", rr.RR_KEY_OCTAHEDRON, rr.RR_T_FIXED, {}),
+                ("two_point_fixed", rr.RR_KEY_TWO_POINT, rr.RR_T_FIXED, {}),
+                ("two_point_adaptive", rr.RR_KEY_TWO_POINT, rr.RR_T_ADAPTIVE, {"table": table}),
+                ("two_point_real", rr.RR_KEY_TWO_POINT, rr.RR_T_GIVEN, {"t_given": tg})]:
+            prm = rr.key_params(layout, 32, lo, hi, t_source=ts, **kw)
+            st_f, pf_f = make_step(B, prm, False, bits=32)
+            _, _, ph_f = timed(st_f, kf, 3, pf_f)
+            tr = float(np.median(np.array(ph_f)[:, 3]))
+            fam[name] = {"trace_ms": round(tr, 4), "trace_speedup": round(t_uns_ms / tr, 3),
+                         "capsule_rel": round(capsule_mean(B["so"], B["sd"], B["hits"]) / coherence["unsorted"], 3)}
+        extra["key_families_32bit"] = fam
+
         # cheaper reorderings of the same bounce (local sort, indirect access)
         variants = {}
         kv = max(3, args.steps // 2)
+        params_costa32 = rr.key_params(rr.RR_KEY_COSTA, 32, lo, hi)
         for name, kw in [("global64_indirect", dict(params=params_tp, accumulate=True, reorder="indirect")),
+                         ("costa32_gather", dict(params=params_costa32, accumulate=False, bits=32)),
+                         ("costa32_indirect", dict(params=params_costa32, accumulate=False, bits=32,
+                                                   reorder="indirect")),
                          ("global32_indirect", dict(params=params_tp32, accumulate=True, bits=32, reorder="indirect")),
                          ("local1024_indirect", dict(params=params_tp, accumulate=True, sort="segment", segment=1024,
                                                      reorder="indirect")),
@@ -383,6 +409,9 @@ def run_ours(args):
                               "phases_ms": {k: round(float(v), 4) for k, v in
                                             zip(["key", "sort", "gather", "trace"], med[:4])}}
         extra["reorder_variants"] = variants
+        best = max(variants, key=lambda k: variants[k]["mrays"])
+        extra["best_reorder"] = {"variant": best, "mrays": variants[best]["mrays"],
+                                 "vs_unsorted": round(variants[best]["mrays"] / unsorted, 3)}
         if rr.rr_device_error() != 0:
             raise RuntimeError("device error flag set during the reorder variants")
 
