@@ -690,9 +690,39 @@ def run_sweep(args):
                          "sort_frac_hbm": round(sort_bytes / (float(ph[1]) * 1e-3) / 1e9 / hbm, 3)})
             del ws
         del keys
+    # the direction-first Costa key (32 bits) with the gather and with indirect access
+    keys32 = torch.empty(n, dtype=torch.int32, device=dev)
+    ws32 = rr.sort_workspace(n, 32, 8, dev)
+    params_c = rr.key_params(rr.RR_KEY_COSTA, 32, lo, hi)
+    extra_rows = {}
+    for reorder in ("gather", "indirect"):
+        def step_c(evs):
+            if evs:
+                evs[0].record(stream)
+            rr.rr_compute_keys(o, d, params_c, keys32)
+            if evs:
+                evs[1].record(stream)
+            rr.rr_sort(keys32, None, perm, n, 32, 8, ws32)
+            if evs:
+                evs[2].record(stream)
+            if reorder == "gather":
+                rr.rr_permute(o, d, p, perm, so, sd, sp)
+                if evs:
+                    evs[3].record(stream)
+                rr.rr_trace(bvh, so, sd, hits)
+            else:
+                if evs:
+                    evs[3].record(stream)
+                rr.rr_trace_ex(bvh, o, d, hits, order=perm)
+            if evs:
+                evs[4].record(stream)
+        ph = timed(step_c, 5)
+        extra_rows["costa32_" + reorder] = {
+            "key_ms": round(float(ph[0]), 4), "sort_ms": round(float(ph[1]), 4), "gather_ms": round(float(ph[2]), 4),
+            "trace_ms": round(float(ph[3]), 4), "sorted_e2e_mrays": round(n / (float(ph.sum()) * 1e-3) / 1e6, 1)}
     if rr.rr_device_error() != 0:
         raise RuntimeError("device error flag set during the sweep")
-    out = {"metric": METRIC, "sweep": rows, "unit": UNIT,
+    out = {"metric": METRIC, "sweep": rows, "costa": extra_rows, "unit": UNIT,
            "config": {"workload": "scale sweep: %d-triangle terrain, %dx%d bounce-2 wavefront (%d rays); Two Point "
                                   "key (adaptive estimate)" % (tris.shape[0], cam.width, cam.height, n),
                       "l2": "flushed between steps (256 MB write)"},
