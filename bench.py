@@ -779,6 +779,8 @@ def bench_batched(args, dev, flush):
     # the reordered batch: the tuner's choice, or the best sorted candidate
     # when the tuner found that not reordering was faster
     cfg = tuned if tuned.key_bits else rr.Batch.config(24, 8, tuned.trace_block)
+    layout_names = {-1: "two_point (the batch's own)", rr.RR_KEY_COSTA: "costa",
+                    rr.RR_KEY_AILA_COMPACT: "aila_compact"}
     tune_s = time.time() - t0
     stream = torch.cuda.current_stream()
 
@@ -810,7 +812,7 @@ def bench_batched(args, dev, flush):
             a, b_ = offs[k], offs[k + 1]
             rr.rr_trace(fronts[k][0], o[a:b_], d[a:b_], hits[a:b_])
     ms_uns = timed(unsorted, K)
-    cfg0 = rr.Batch.config(0, 8, cfg.trace_block)
+    cfg0 = rr.Batch.config(0, 8, cfg.trace_block, cfg.layout)
     ms_graph0 = timed(lambda: batch.run(o, d, hits, cfg0), K)
     if rr.rr_device_error() != 0:
         raise RuntimeError("device error flag set during the batched measurement")
@@ -818,10 +820,11 @@ def bench_batched(args, dev, flush):
                        "key (fixed estimate)" % (BATCH_WAVEFRONTS, int(1e4 * scale), int(2e6 * scale),
                                                  len(scenes), "/".join(str(t.shape[0]) for t in scenes)),
            "rays": int(n), "autotuned": {"key_bits": tuned.key_bits, "radix_bits": tuned.radix_bits,
-                                          "trace_block": tuned.trace_block, "tuned_ms": round(tuned_ms, 3),
-                                          "tune_s": round(tune_s, 2)},
+                                          "trace_block": tuned.trace_block,
+                                          "layout": layout_names.get(tuned.layout, tuned.layout),
+                                          "tuned_ms": round(tuned_ms, 3), "tune_s": round(tune_s, 2)},
            "sorted_config": {"key_bits": cfg.key_bits, "radix_bits": cfg.radix_bits,
-                             "trace_block": cfg.trace_block},
+                             "trace_block": cfg.trace_block, "layout": layout_names.get(cfg.layout, cfg.layout)},
            "graph_ms": round(ms_graph, 3), "graph_mrays": round(n / (ms_graph * 1e-3) / 1e6, 1),
            "graph_kernels": 3 + -(-(cfg.key_bits + batch.info()["seg_bits"]) // cfg.radix_bits),
            "loop_ms": round(ms_loop, 3), "loop_mrays": round(n / (ms_loop * 1e-3) / 1e6, 1),

@@ -396,6 +396,9 @@ typedef struct {
                               perm_out not written) */
     uint32_t radix_bits;   /* 4 or 8 */
     uint32_t trace_block;  /* threads per trace block: 128, 256 or 512 */
+    int32_t layout;        /* key layout of this run (an rr_key_layout), or -1 for the batch's own
+                              layout and estimate; another layout only orders the rays (Two Point
+                              then takes the FIXED estimate) and the tables are still updated */
 } rr_batch_config;
 
 typedef struct rr_batch rr_batch;
@@ -437,10 +440,11 @@ rr_status rr_batch_run_loop(rr_batch *batch, const float *o_tmin, const float *d
                             uint32_t *perm_out, const rr_batch_config *cfg, void *stream);
 
 /*
- * rr_batch_tune - autotuner: times rr_batch_run on these buffers for key bits
- * {12, 16, 20, 24, 32, 48, 64} (capped by the wavefront bits) x radix width {4, 8}
- * and for no reordering (key bits 0) at 256-thread trace blocks, then trace
- * blocks of 128 and 512 for the winner,
+ * rr_batch_tune - autotuner: times rr_batch_run on these buffers for the key
+ * layouts {the batch's own, Costa, Aila Compact} x key bits {12, 16, 20, 24, 32,
+ * 48, 64} (capped by the wavefront bits) x radix width {4, 8}, and for no
+ * reordering (key bits 0), at 256-thread trace blocks, then trace blocks of 128
+ * and 512 for the winner,
  * and returns the fastest configuration (mean of 3 timed runs after one
  * warm-up) and its time.  Length tables are saved before and restored after,
  * so tuning leaves them as it found them.  Synchronising.

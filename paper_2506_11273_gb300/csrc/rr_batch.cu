@@ -37,11 +37,13 @@ uint32_t bits_for(uint32_t n) {  // bits that number 0..n-1
 
 bool config_ok(const rr_batch_config *c, uint32_t seg_bits) {
     return c && c->key_bits + seg_bits <= 64 && (c->radix_bits == 4 || c->radix_bits == 8) &&
+           c->layout >= -1 && c->layout <= (int32_t)RR_KEY_OCTAHEDRON &&
            (c->trace_block == 128 || c->trace_block == 256 || c->trace_block == 512);
 }
 
 bool same_cfg(const rr_batch_config &a, const rr_batch_config &b) {
-    return a.key_bits == b.key_bits && a.radix_bits == b.radix_bits && a.trace_block == b.trace_block;
+    return a.key_bits == b.key_bits && a.radix_bits == b.radix_bits && a.trace_block == b.trace_block &&
+           a.layout == b.layout;
 }
 
 }  // namespace
@@ -71,13 +73,24 @@ namespace {
 
 bool accumulating(const rr_batch *b) { return b->layout == RR_KEY_TWO_POINT && b->tsrc == RR_T_ADAPTIVE; }
 
+// The layout and estimate a configuration keys with: the batch's own, or
+// another layout that only orders the rays (Two Point with the FIXED estimate).
+rr_key_layout run_layout(const rr_batch *b, const rr_batch_config &c) {
+    return c.layout < 0 ? b->layout : (rr_key_layout)c.layout;
+}
+rr_t_source run_tsrc(const rr_batch *b, const rr_batch_config &c) {
+    const rr_key_layout l = run_layout(b, c);
+    return l == RR_KEY_TWO_POINT && l == b->layout ? b->tsrc : RR_T_FIXED;
+}
+
 // The whole chain on one stream: keys, sort, trace.
 rr_status enqueue_batch(rr_batch *b, const float *o, const float *d, float *hits, uint32_t *perm,
                         const rr_batch_config &c, cudaStream_t s) {
     if (c.key_bits == 0)  // no reordering: every ray traced in input order
         return launch_trace_batch(b->d_segs, b->d_offsets, b->n_fronts, o, d, nullptr, b->n_total, hits,
                                   accumulating(b), c.trace_block, b->queue, s);
-    rr_status st = launch_keys_batch(b->d_segs, b->d_offsets, b->n_fronts, b->layout, b->tsrc, b->ratio, c.key_bits,
+    rr_status st = launch_keys_batch(b->d_segs, b->d_offsets, b->n_fronts, run_layout(b, c), run_tsrc(b, c), b->ratio,
+                                     c.key_bits,
                                      b->seg_bits, o, d, b->n_total, b->keys, s);
     if (st != RR_OK) return st;
     st = rr_sort(b->keys, nullptr, perm, b->n_total, c.key_bits + b->seg_bits, c.radix_bits, b->sort_ws,
@@ -300,15 +313,15 @@ extern "C" rr_status rr_batch_run_loop(rr_batch *b, const float *o_tmin, const f
         const rr_wavefront &f = b->fronts[k];
         if (f.count == 0) continue;
         rr_key_params p{};
-        p.layout = b->layout;
+        p.layout = run_layout(b, *cfg);
         p.bits = cfg->key_bits;
-        p.t_source = b->tsrc;
+        p.t_source = run_tsrc(b, *cfg);
         p.ratio = b->ratio;
         for (int c = 0; c < 3; ++c) {
             p.aabb_lo[c] = f.aabb_lo[c];
             p.aabb_hi[c] = f.aabb_hi[c];
         }
-        p.table = accumulating(b) ? f.table : nullptr;
+        p.table = p.t_source == RR_T_ADAPTIVE ? f.table : nullptr;
         st = rr_compute_keys(o_tmin + 4ull * f.offset, d_tmax + 4ull * f.offset, f.count, &p, keys + kb * f.offset,
                              stream);
         if (st != RR_OK) return st;
@@ -333,7 +346,7 @@ extern "C" rr_status rr_batch_run_loop(rr_batch *b, const float *o_tmin, const f
 extern "C" rr_status rr_batch_tune(rr_batch *b, const float *o_tmin, const float *d_tmax, float *hits_out,
                                    rr_batch_config *best, float *best_ms, void *stream) {
     if (!b || !best) return fail(RR_ERR_INVALID_ARG, "rr_batch_tune: NULL argument");
-    rr_batch_config probe{16, 8, 256};
+    rr_batch_config probe{16, 8, 256, -1};
     rr_status st = check_run_args(b, o_tmin, d_tmax, hits_out, &probe, "rr_batch_tune");
     if (st != RR_OK) return st;
     cudaStream_t s = as_stream(stream);
@@ -374,21 +387,28 @@ extern "C" rr_status rr_batch_tune(rr_batch *b, const float *o_tmin, const float
     // key bits x radix width at the default block (0 bits: no reordering), then
     // the block for the winner
     const uint32_t cand_bits[] = {0, 12, 16, 20, 24, 32, 48, 64};
-    rr_batch_config win{0, 0, 0};
+    std::vector<int32_t> cand_layouts{-1};
+    for (rr_key_layout l : {RR_KEY_COSTA, RR_KEY_AILA_COMPACT})
+        if (l != b->layout) cand_layouts.push_back((int32_t)l);
+    rr_batch_config win{0, 0, 0, -1};
     float win_ms = -1.0f;
     st = RR_OK;
-    for (uint32_t kb : cand_bits) {
-        const uint32_t bits = std::min(kb, 64u - b->seg_bits);
-        for (uint32_t rb : {4u, 8u}) {
-            if (kb == 0 && rb == 4) continue;  // nothing is sorted
-            const rr_batch_config c{bits, rb, 256};
-            float ms = 0.0f;
-            st = time_cfg(c, &ms);
-            if (st != RR_OK) break;
-            if (win_ms < 0.0f || ms < win_ms) {
-                win = c;
-                win_ms = ms;
+    for (int32_t lay : cand_layouts) {
+        for (uint32_t kb : cand_bits) {
+            if (kb == 0 && lay != -1) continue;  // no reordering is tried once
+            const uint32_t bits = std::min(kb, 64u - b->seg_bits);
+            for (uint32_t rb : {4u, 8u}) {
+                if (kb == 0 && rb == 4) continue;  // nothing is sorted
+                const rr_batch_config c{bits, rb, 256, lay};
+                float ms = 0.0f;
+                st = time_cfg(c, &ms);
+                if (st != RR_OK) break;
+                if (win_ms < 0.0f || ms < win_ms) {
+                    win = c;
+                    win_ms = ms;
+                }
             }
+            if (st != RR_OK) break;
         }
         if (st != RR_OK) break;
     }

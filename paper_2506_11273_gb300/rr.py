@@ -73,10 +73,11 @@ class Wavefront(C.Structure):
 
 
 class BatchConfig(C.Structure):
-    _fields_ = [("key_bits", C.c_uint32), ("radix_bits", C.c_uint32), ("trace_block", C.c_uint32)]
+    _fields_ = [("key_bits", C.c_uint32), ("radix_bits", C.c_uint32), ("trace_block", C.c_uint32),
+                ("layout", C.c_int32)]
 
     def as_tuple(self):
-        return (int(self.key_bits), int(self.radix_bits), int(self.trace_block))
+        return (int(self.key_bits), int(self.radix_bits), int(self.trace_block), int(self.layout))
 
 
 class ServerConfig(C.Structure):
@@ -450,8 +451,8 @@ class Batch:
         return dict(n_rays=n.value, seg_bits=sb.value, graphs=g.value)
 
     @staticmethod
-    def config(key_bits: int, radix_bits: int = 8, trace_block: int = 256) -> BatchConfig:
-        return BatchConfig(key_bits, radix_bits, trace_block)
+    def config(key_bits: int, radix_bits: int = 8, trace_block: int = 256, layout: int = -1) -> BatchConfig:
+        return BatchConfig(key_bits, radix_bits, trace_block, layout)
 
     def run(self, o_tmin, d_tmax, hits_out, cfg: BatchConfig, perm_out=None, stream=None):
         _check(lib().rr_batch_run(self.handle, _ptr(o_tmin), _ptr(d_tmax), _ptr(hits_out), _ptr(perm_out),

@@ -189,7 +189,7 @@ def test_batch_adaptive_tables(world):
     # the autotuner leaves the tables as it found them and picks a valid config
     best, ms = b.tune(o, d, h2)
     assert best.radix_bits in (4, 8) and best.trace_block in (128, 256, 512)
-    assert 0 <= best.key_bits <= 60 and ms > 0
+    assert 0 <= best.key_bits <= 60 and ms > 0 and best.layout in (-1, rr.RR_KEY_COSTA, rr.RR_KEY_AILA_COMPACT)
     for t, (sm, cn) in zip(tables, after_graph):
         s2, c2 = t.read()
         assert np.array_equal(s2, sm) and np.array_equal(c2, cn)
@@ -258,3 +258,30 @@ def test_batch_degenerate_shapes(world):
     empty.run(o, d, h, rr.Batch.config(16, 8, 256))  # nothing to do
     empty.close()
     assert rr.rr_device_error() == 0
+
+
+def test_batch_config_layout_overrides_the_key(world):
+    """A configuration's layout orders the rays with another key family (Two
+    Point falls back to the FIXED estimate); graph and loop agree; hits stay."""
+    b = make_batch(world, rr.RR_KEY_TWO_POINT)
+    o, d = _dev(world["o"]), _dev(world["d"])
+    n = b.n
+    base = torch.empty(n, 4, device="cuda")
+    b.run(o, d, base, rr.Batch.config(24, 8, 256))
+    for layout, olayout, bits in [(rr.RR_KEY_COSTA, oracle.COSTA, 28), (rr.RR_KEY_AILA_COMPACT, oracle.AILA_COMPACT, 40)]:
+        hits = torch.empty(n, 4, device="cuda")
+        perm = torch.empty(n, dtype=torch.int32, device="cuda")
+        cfg = rr.Batch.config(bits, 8, 256, layout)
+        b.run(o, d, hits, cfg, perm)
+        p_or, _, _ = oracle_batch(world, olayout, bits)
+        assert np.array_equal(rr.u32_to_numpy(perm), p_or)
+        assert np.array_equal(_bits(hits.cpu().numpy()), _bits(base.cpu().numpy()))
+        p2 = torch.empty(n, dtype=torch.int32, device="cuda")
+        b.run_loop(o, d, hits, cfg, p2)
+        assert np.array_equal(local_to_global(rr.u32_to_numpy(p2)), p_or)
+    with pytest.raises(rr.RRError):
+        b.run(o, d, base, rr.Batch.config(24, 8, 256, 9))
+    best, _ = b.tune(o, d, base)
+    assert best.layout in (-1, rr.RR_KEY_COSTA, rr.RR_KEY_AILA_COMPACT)
+    assert rr.rr_device_error() == 0
+    b.close()
