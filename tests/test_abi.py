@@ -66,3 +66,35 @@ def test_product_path_never_imports_the_oracle():
                 text = open(os.path.join(dirpath, f), errors="replace").read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), f
                 assert "liboracle" not in text and "oracle.c" not in text, f
+
+
+def test_host_argument_checks_without_a_gpu(librr):
+    """Entry points that need no device answer on the host: workspace sizes
+    follow the documented layout and bad arguments are refused before any
+    device work; calls that need a device fail with a status, not a crash."""
+    lib = ctypes.CDLL(librr)
+    lib.rr_sort_workspace_size.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                           ctypes.POINTER(ctypes.c_size_t)]
+    size = ctypes.c_size_t()
+    prev = 0
+    for n in (1, 1000, 4096, 4097, 1 << 20, 8294400):
+        for bits, radix in ((32, 8), (64, 8), (64, 4), (16, 4)):
+            assert lib.rr_sort_workspace_size(n, bits, radix, ctypes.byref(size)) == 0
+            kb = 8 if bits > 32 else 4
+            passes = -(-bits // radix)
+            # two key buffers and one value buffer, plus counts and look-back words
+            assert size.value >= 2 * kb * n + 4 * n + passes * (1 << radix) * 4
+        assert lib.rr_sort_workspace_size(n, 64, 8, ctypes.byref(size)) == 0
+        assert size.value >= prev
+        prev = size.value
+    for bits, radix, n in ((0, 8, 10), (65, 8, 10), (32, 5, 10), (32, 8, 1 << 30)):
+        assert lib.rr_sort_workspace_size(n, bits, radix, ctypes.byref(size)) == 1  # RR_ERR_INVALID_ARG
+    lib.rr_compute_keys.argtypes = [ctypes.c_void_p] * 2 + [ctypes.c_uint32] + [ctypes.c_void_p] * 3
+    assert lib.rr_compute_keys(None, None, 10, None, None, None) == 1  # NULL params: refused first
+    import torch
+    if not torch.cuda.is_available():
+        lib.rr_build_bvh.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)]
+        tri = (ctypes.c_float * 9)(0, 0, 0, 1, 0, 0, 0, 1, 0)
+        h = ctypes.c_void_p()
+        assert lib.rr_build_bvh(tri, 1, ctypes.byref(h)) == 2  # RR_ERR_CUDA: no device, no crash
+        assert not h.value
