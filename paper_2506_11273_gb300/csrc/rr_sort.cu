@@ -38,6 +38,16 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
+// Programmatic dependent launch: a pass lets the next kernel of its stream
+// start its blocks once all of its own have started, and waits (before it
+// touches global memory) until the kernel before it has finished and its
+// writes are visible.  Both are no-ops for a kernel launched without the
+// programmatic-serialisation attribute.
+__device__ __forceinline__ void allow_dependent_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void wait_for_prerequisite() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <typename K>
 struct SortTile;
 template <>
@@ -107,6 +117,7 @@ __global__ void __launch_bounds__(kSortBlock) sort_histogram_kernel(const K *__r
     constexpr int PMAX = (64 + RBITS - 1) / RBITS;
     constexpr int KPT = 4;  // keys per thread per round
     __shared__ uint32_t sh[2][PMAX * RADIX];
+    allow_dependent_launch();
     for (uint32_t i = threadIdx.x; i < 2 * PMAX * RADIX; i += kSortBlock) (&sh[0][0])[i] = 0;
     if (blockIdx.x == 0) {
         if (threadIdx.x < passes) counters[threadIdx.x] = 0u;  // tile counters of every pass
@@ -163,25 +174,37 @@ struct PassArgs {
     uint32_t *err;
 };
 
+// Shared-memory layout of one digit pass.
 template <typename K, int RBITS>
-__global__ void __launch_bounds__(kSortBlock, 3) onesweep_kernel(PassArgs<K> a) {
+struct PassSmem {
+    static constexpr int RADIX = 1 << RBITS;
+    static constexpr int TILE = kSortBlock * SortTile<K>::kItems;
+    // keys [TILE] | values [TILE] | per-warp counters [warps][RADIX] | tile-local
+    // digit starts [RADIX] | global base per digit [RADIX] | tile counts
+    // [RADIX] | misc [16]: [0] tile id, [8..15] scan scratch
+    static constexpr size_t bytes =
+        sizeof(K) * TILE + sizeof(uint32_t) * (TILE + kSortWarps * RADIX + 3 * RADIX + 16);
+};
+static_assert(PassSmem<unsigned long long, 8>::bytes <= 48 * 1024 && PassSmem<uint32_t, 8>::bytes <= 48 * 1024,
+              "a digit pass must fit the default dynamic shared-memory limit");
+
+// One tile of a digit pass.  FULL tiles skip every bounds check; only the
+// last tile of a pass can be partial.
+template <typename K, int RBITS, bool FULL>
+__device__ __forceinline__ void onesweep_tile(const PassArgs<K> &a, uint32_t tile, unsigned char *smem) {
     constexpr int RADIX = 1 << RBITS;
     constexpr int ITEMS = SortTile<K>::kItems;
     constexpr int TILE = kSortBlock * ITEMS;
     constexpr int WTILE = 32 * ITEMS;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    K *s_keys = reinterpret_cast<K *>(smem_raw);
+    K *s_keys = reinterpret_cast<K *>(smem);
     uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + TILE);
-    uint32_t *s_wh = s_vals + TILE;                // [warps][RADIX]: counts, then prefix over warps
+    uint32_t *s_wh = s_vals + TILE;                  // [warps][RADIX]: counts, then prefix over warps
     uint32_t *s_lstart = s_wh + kSortWarps * RADIX;  // tile-local start of each digit
-    uint32_t *s_gbase = s_lstart + RADIX;          // global position minus tile-local position
-    uint32_t *s_misc = s_gbase + RADIX;            // [0] tile id, [8..15] scan scratch
+    uint32_t *s_gbase = s_lstart + RADIX;            // global position minus tile-local position
+    uint32_t *s_cnt = s_gbase + RADIX;               // the tile's count of each digit
+    uint32_t *s_misc = s_cnt + RADIX;
 
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    if (tid == 0) s_misc[0] = atomicAdd(a.tile_counter, 1u);
-    for (uint32_t i = tid; i < kSortWarps * RADIX; i += kSortBlock) s_wh[i] = 0;
-    __syncthreads();
-    const uint32_t tile = s_misc[0];
     const uint32_t base = tile * TILE;
     const uint32_t wbase = base + warp * WTILE;
 
@@ -190,7 +213,7 @@ __global__ void __launch_bounds__(kSortBlock, 3) onesweep_kernel(PassArgs<K> a) 
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const uint32_t idx = wbase + j * 32 + lane;
-        if (idx < a.n) {
+        if (FULL || idx < a.n) {
             k[j] = a.keys_in[idx];
             v[j] = a.vals_in ? a.vals_in[idx] : idx;
         } else {
@@ -198,17 +221,26 @@ __global__ void __launch_bounds__(kSortBlock, 3) onesweep_kernel(PassArgs<K> a) 
             v[j] = 0;
         }
     }
+    // The tile's digit counts, published before the ranking so that later
+    // tiles looking back wait on this tile's loads only, not on its ranking.
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j)
+        if (FULL || wbase + j * 32 + lane < a.n) atomicAdd(&s_cnt[digit_of(k[j], a.shift, a.mask)], 1u);
+    __syncthreads();
+    const uint32_t cnt = tid < RADIX ? s_cnt[tid] : 0u;
+    if (tid < RADIX) st_relaxed(a.lookback + (size_t)tile * RADIX + tid, lookback_word(tile, cnt));
+
     // stable rank inside the warp: items in index order (j, then lane).  The
     // peer masks of every row are independent; only the per-digit counters chain.
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
-        const bool valid = wbase + j * 32 + lane < a.n;
-        r[j] = digit_peers<RBITS>(digit_of(k[j], a.shift, a.mask), __ballot_sync(0xFFFFFFFFu, valid));
+        const uint32_t among = FULL ? 0xFFFFFFFFu : __ballot_sync(0xFFFFFFFFu, wbase + j * 32 + lane < a.n);
+        r[j] = digit_peers<RBITS>(digit_of(k[j], a.shift, a.mask), among);
     }
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
-        const bool valid = wbase + j * 32 + lane < a.n;
+        const bool valid = FULL || wbase + j * 32 + lane < a.n;
         const uint32_t dg = digit_of(k[j], a.shift, a.mask);
         const uint32_t peers = r[j];
         const uint32_t cur = valid ? s_wh[warp * RADIX + dg] : 0u;
@@ -219,15 +251,15 @@ __global__ void __launch_bounds__(kSortBlock, 3) onesweep_kernel(PassArgs<K> a) 
     }
     __syncthreads();
 
-    // per digit: prefix over warps and the tile's count, published at once
-    uint32_t cnt = 0;
+    // per digit: prefix over warps
     if (tid < RADIX) {
+        uint32_t acc = 0;
+#pragma unroll
         for (int w = 0; w < kSortWarps; ++w) {
             const uint32_t c = s_wh[w * RADIX + tid];
-            s_wh[w * RADIX + tid] = cnt;
-            cnt += c;
+            s_wh[w * RADIX + tid] = acc;
+            acc += c;
         }
-        st_relaxed(a.lookback + (size_t)tile * RADIX + tid, lookback_word(tile, cnt));
     }
     const uint32_t dstart = scan_digits<RADIX>(tid < RADIX ? a.hist[tid] : 0u, s_misc + 8);
     const uint32_t lstart = scan_digits<RADIX>(cnt, s_misc + 8);
@@ -264,7 +296,7 @@ __global__ void __launch_bounds__(kSortBlock, 3) onesweep_kernel(PassArgs<K> a) 
     // scatter into shared memory in digit order (stable)
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
-        if (wbase + j * 32 + lane < a.n) {
+        if (FULL || wbase + j * 32 + lane < a.n) {
             const uint32_t dg = digit_of(k[j], a.shift, a.mask);
             const uint32_t pos = s_lstart[dg] + s_wh[warp * RADIX + dg] + r[j];
             s_keys[pos] = k[j];
@@ -272,13 +304,45 @@ __global__ void __launch_bounds__(kSortBlock, 3) onesweep_kernel(PassArgs<K> a) 
         }
     }
     __syncthreads();
-    const uint32_t tile_n = min((uint32_t)TILE, a.n - base);
-    for (uint32_t i = tid; i < tile_n; i += kSortBlock) {
-        const K key = s_keys[i];
-        const uint32_t gpos = s_gbase[digit_of(key, a.shift, a.mask)] + i;
-        if (a.keys_out) a.keys_out[gpos] = key;
-        a.vals_out[gpos] = s_vals[i];
+    // global writes in tile order: runs of equal digits land contiguously
+    if (FULL) {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const uint32_t i = j * kSortBlock + tid;
+            const K key = s_keys[i];
+            const uint32_t gpos = s_gbase[digit_of(key, a.shift, a.mask)] + i;
+            if (a.keys_out) a.keys_out[gpos] = key;
+            a.vals_out[gpos] = s_vals[i];
+        }
+    } else {
+        const uint32_t tile_n = min((uint32_t)TILE, a.n - base);
+        for (uint32_t i = tid; i < tile_n; i += kSortBlock) {
+            const K key = s_keys[i];
+            const uint32_t gpos = s_gbase[digit_of(key, a.shift, a.mask)] + i;
+            if (a.keys_out) a.keys_out[gpos] = key;
+            a.vals_out[gpos] = s_vals[i];
+        }
     }
+}
+
+template <typename K, int RBITS>
+__global__ void __launch_bounds__(kSortBlock, 3) onesweep_kernel(PassArgs<K> a) {
+    using L = PassSmem<K, RBITS>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *s_wh = reinterpret_cast<uint32_t *>(smem_raw + sizeof(K) * L::TILE) + L::TILE;
+    uint32_t *s_cnt = s_wh + kSortWarps * L::RADIX + 2 * L::RADIX;
+    uint32_t *s_misc = s_cnt + L::RADIX;
+    allow_dependent_launch();
+    for (uint32_t i = threadIdx.x; i < kSortWarps * L::RADIX; i += kSortBlock) s_wh[i] = 0;
+    for (uint32_t i = threadIdx.x; i < (uint32_t)L::RADIX; i += kSortBlock) s_cnt[i] = 0;
+    wait_for_prerequisite();
+    if (threadIdx.x == 0) s_misc[0] = atomicAdd(a.tile_counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_misc[0];
+    if ((tile + 1) * (uint32_t)L::TILE <= a.n)
+        onesweep_tile<K, RBITS, true>(a, tile, smem_raw);
+    else
+        onesweep_tile<K, RBITS, false>(a, tile, smem_raw);
 }
 
 // ------------------------------------------------------------------ local (segment) sort
@@ -442,9 +506,24 @@ constexpr SortPlan plan_sort(uint32_t n, uint32_t bits, uint32_t radix_bits) {
 
 template <typename K, int RBITS>
 static size_t pass_smem() {
-    constexpr int RADIX = 1 << RBITS;
-    constexpr int TILE = kSortBlock * SortTile<K>::kItems;
-    return sizeof(K) * TILE + sizeof(uint32_t) * (TILE + kSortWarps * RADIX + 2 * RADIX + 16);
+    return PassSmem<K, RBITS>::bytes;
+}
+
+// One digit pass, launched so that it may start while the kernel before it
+// drains (programmatic dependent launch; the pass waits in the kernel).
+template <typename K, int RBITS>
+static cudaError_t launch_pass(const PassArgs<K> &a, uint32_t tiles, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(tiles);
+    cfg.blockDim = dim3(kSortBlock);
+    cfg.dynamicSmemBytes = pass_smem<K, RBITS>();
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, onesweep_kernel<K, RBITS>, a);
 }
 
 // Enqueues the whole sort: counting pass, one kernel per digit pass.
@@ -469,7 +548,6 @@ static cudaError_t enqueue_sort(const SortPlan &pl, const K *keys_in, K *keys_ou
         1u, std::min({(n + per_block - 1) / per_block, 2u * (uint32_t)sm_count, kHistMaxBlocks}));
     sort_histogram_kernel<K, RBITS><<<hist_blocks, kSortBlock, 0, s>>>(
         keys_in, n, bits, pl.passes, hist, reinterpret_cast<uint4 *>(lookback), zero_count, counters, zero_err);
-    const size_t smem = pass_smem<K, RBITS>();
     const K *kin = keys_in;
     const uint32_t *vin = nullptr;
     for (uint32_t p = 0; p < pl.passes; ++p) {
@@ -493,7 +571,8 @@ static cudaError_t enqueue_sort(const SortPlan &pl, const K *keys_in, K *keys_ou
         a.lookback = lookback + (size_t)p * pl.tiles * pl.radix;
         a.tile_counter = counters + p;
         a.err = err;
-        onesweep_kernel<K, RBITS><<<pl.tiles, kSortBlock, smem, s>>>(a);
+        e = launch_pass<K, RBITS>(a, pl.tiles, s);
+        if (e != cudaSuccess) return e;
         kin = kout;
         vin = vout;
     }
