@@ -1,10 +1,11 @@
 // Stable LSD radix sort of (key, index) pairs (Section 3.2), onesweep style:
 // one upfront pass counts the digits of every pass; then each digit pass is a
-// single kernel in which a tile ranks its keys (peer masks from warp votes),
-// publishes its per-digit counts, resolves its global offsets by a
-// decoupled look-back over the preceding tiles (pointer jumping over
-// published spans), and scatters through shared memory so that global writes come out
-// in runs.
+// single kernel in which a tile counts its digits and publishes the counts,
+// ranks its keys (peer masks from warp votes), resolves its global offsets by
+// a decoupled look-back over the preceding tiles (pointer jumping over
+// published spans), and scatters through shared memory so that global writes
+// come out in runs.  Consecutive passes overlap launch and drain
+// (programmatic dependent launch).
 #include <algorithm>
 #include <mutex>
 
@@ -189,8 +190,10 @@ static_assert(PassSmem<unsigned long long, 8>::bytes <= 48 * 1024 && PassSmem<ui
               "a digit pass must fit the default dynamic shared-memory limit");
 
 // One tile of a digit pass.  FULL tiles skip every bounds check; only the
-// last tile of a pass can be partial.
-template <typename K, int RBITS, bool FULL>
+// last tile of a pass can be partial.  LATE loads the values after the
+// ranking (their loads then overlap the look-back), which keeps the ranking's
+// registers low enough for four blocks per SM.
+template <typename K, int RBITS, bool FULL, bool LATE>
 __device__ __forceinline__ void onesweep_tile(const PassArgs<K> &a, uint32_t tile, unsigned char *smem) {
     constexpr int RADIX = 1 << RBITS;
     constexpr int ITEMS = SortTile<K>::kItems;
@@ -215,10 +218,10 @@ __device__ __forceinline__ void onesweep_tile(const PassArgs<K> &a, uint32_t til
         const uint32_t idx = wbase + j * 32 + lane;
         if (FULL || idx < a.n) {
             k[j] = a.keys_in[idx];
-            v[j] = a.vals_in ? a.vals_in[idx] : idx;
+            if (!LATE) v[j] = a.vals_in ? a.vals_in[idx] : idx;
         } else {
             k[j] = 0;
-            v[j] = 0;
+            if (!LATE) v[j] = 0;
         }
     }
     // The tile's digit counts, published before the ranking so that later
@@ -250,6 +253,13 @@ __device__ __forceinline__ void onesweep_tile(const PassArgs<K> &a, uint32_t til
         r[j] = cur + __popc(peers & lt);
     }
     __syncthreads();
+    if (LATE) {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const uint32_t idx = wbase + j * 32 + lane;
+            v[j] = (FULL || idx < a.n) ? (a.vals_in ? a.vals_in[idx] : idx) : 0u;
+        }
+    }
 
     // per digit: prefix over warps
     if (tid < RADIX) {
@@ -325,8 +335,10 @@ __device__ __forceinline__ void onesweep_tile(const PassArgs<K> &a, uint32_t til
     }
 }
 
-template <typename K, int RBITS>
-__global__ void __launch_bounds__(kSortBlock, 3) onesweep_kernel(PassArgs<K> a) {
+// MINB blocks per SM: 3 for passes of one wave or less (shortest tile
+// latency), 4 with late values for longer passes (more tiles in flight).
+template <typename K, int RBITS, int MINB>
+__global__ void __launch_bounds__(kSortBlock, MINB) onesweep_kernel(PassArgs<K> a) {
     using L = PassSmem<K, RBITS>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t *s_wh = reinterpret_cast<uint32_t *>(smem_raw + sizeof(K) * L::TILE) + L::TILE;
@@ -340,9 +352,9 @@ __global__ void __launch_bounds__(kSortBlock, 3) onesweep_kernel(PassArgs<K> a) 
     __syncthreads();
     const uint32_t tile = s_misc[0];
     if ((tile + 1) * (uint32_t)L::TILE <= a.n)
-        onesweep_tile<K, RBITS, true>(a, tile, smem_raw);
+        onesweep_tile<K, RBITS, true, (MINB > 3)>(a, tile, smem_raw);
     else
-        onesweep_tile<K, RBITS, false>(a, tile, smem_raw);
+        onesweep_tile<K, RBITS, false, (MINB > 3)>(a, tile, smem_raw);
 }
 
 // ------------------------------------------------------------------ local (segment) sort
@@ -511,8 +523,9 @@ static size_t pass_smem() {
 
 // One digit pass, launched so that it may start while the kernel before it
 // drains (programmatic dependent launch; the pass waits in the kernel).
+// Passes of at least two waves at four blocks per SM take the four-block form.
 template <typename K, int RBITS>
-static cudaError_t launch_pass(const PassArgs<K> &a, uint32_t tiles, cudaStream_t s) {
+static cudaError_t launch_pass(const PassArgs<K> &a, uint32_t tiles, int sm_count, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(tiles);
     cfg.blockDim = dim3(kSortBlock);
@@ -523,7 +536,8 @@ static cudaError_t launch_pass(const PassArgs<K> &a, uint32_t tiles, cudaStream_
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, onesweep_kernel<K, RBITS>, a);
+    if (tiles >= 8u * (uint32_t)sm_count) return cudaLaunchKernelEx(&cfg, onesweep_kernel<K, RBITS, 4>, a);
+    return cudaLaunchKernelEx(&cfg, onesweep_kernel<K, RBITS, 3>, a);
 }
 
 // Enqueues the whole sort: counting pass, one kernel per digit pass.
@@ -571,7 +585,7 @@ static cudaError_t enqueue_sort(const SortPlan &pl, const K *keys_in, K *keys_ou
         a.lookback = lookback + (size_t)p * pl.tiles * pl.radix;
         a.tile_counter = counters + p;
         a.err = err;
-        e = launch_pass<K, RBITS>(a, pl.tiles, s);
+        e = launch_pass<K, RBITS>(a, pl.tiles, sm_count, s);
         if (e != cudaSuccess) return e;
         kin = kout;
         vin = vout;
@@ -708,7 +722,7 @@ extern "C" rr_status rr_selftest_lookback_timeout(void *stream) {
         a.lookback = reinterpret_cast<unsigned long long *>(ws + pl.off_lookback);
         a.tile_counter = counter;
         a.err = ds->err;
-        onesweep_kernel<K, 8><<<1, kSortBlock, pass_smem<K, 8>(), s>>>(a);
+        onesweep_kernel<K, 8, 3><<<1, kSortBlock, pass_smem<K, 8>(), s>>>(a);
         note_launches(1);
         e = cudaGetLastError();
     }
