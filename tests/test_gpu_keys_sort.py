@@ -209,6 +209,25 @@ def test_sort_matches_oracle(radix_bits, bits, n):
     assert_no_device_error()
 
 
+@pytest.mark.parametrize("radix_bits", [8, 4])
+@pytest.mark.parametrize("bits", [32, 64])
+def test_sort_long_passes_match_oracle(radix_bits, bits):
+    """Passes of at least eight tiles per SM take the four-blocks-per-SM form
+    (values loaded after the ranking); just below that they take the
+    three-block form.  Both sides of the switch, with a one-key ragged tail
+    and repeated keys, against the oracle."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    tile = 256 * (12 if bits > 32 else 16)
+    rng = np.random.default_rng(77 + bits + radix_bits)
+    for tiles in (8 * sms - 1, 8 * sms + 1):
+        n = (tiles - 1) * tile + 1
+        keys = _random_keys(n, bits, rng, dup=tiles > 8 * sms)
+        perm_or, _ = oracle.stable_sort(keys)
+        perm, _ = gpu_sort(keys, bits, radix_bits, want_keys=False)
+        assert np.array_equal(perm, perm_or), (tiles, n)
+    assert_no_device_error()
+
+
 @pytest.mark.parametrize("bits", [32, 64])
 def test_sort_without_key_output_and_determinism(bits):
     rng = np.random.default_rng(5)
