@@ -337,9 +337,16 @@ rr_status rr_pipeline_run(rr_pipeline *p, const float *o_tmin, const float *d_tm
                           uint32_t *payload_out, void *stream);
 
 /*
- * rr_pipeline_run_host - host buffers (pinned for full copy speed): copies the
- * rays to the device, runs the bounce, copies hits and payloads back, and
- * synchronises `stream` before returning.
+ * rr_pipeline_run_host - host buffers (page-locked for full speed): copies the
+ * rays to the device, runs the bounce, returns hits and payloads, and
+ * synchronises `stream` (and the handle's side stream) before returning.
+ * Payloads move on a side stream, overlapped with the key, sort and trace
+ * kernels.  When hits_host is page-locked host memory (cudaHostAlloc or
+ * cudaHostRegister) over its whole n * 16 bytes and 16-byte aligned, the trace
+ * kernel stores the hits there directly, so their transfer overlaps the trace;
+ * otherwise they are staged on the device and copied back.  Both forms give
+ * the same bytes.  A hits_host whose first and last bytes are page-locked must
+ * be page-locked in between (one allocation).
  */
 rr_status rr_pipeline_run_host(rr_pipeline *p, const float *o_tmin_host, const float *d_tmax_host,
                                const uint32_t *payload_host, uint32_t n, float *hits_host,

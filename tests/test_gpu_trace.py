@@ -208,7 +208,11 @@ def test_pipeline_matches_oracle_config1(name, layout, olayout, bits, tsrc, otsr
     o, d, p = rr.to_device_rays(rays)
     hits = torch.empty(len(rays), 4, device="cuda")
     pout = torch.empty_like(p)
-    for entry in ("device", "host"):
+    n = len(rays)
+    # host entries: pageable buffers (copies), page-locked buffers (the trace
+    # stores hits straight into host memory), page-locked hits at an offset
+    # inside their allocation with pageable payloads (mixed)
+    for entry in ("device", "host", "host_pinned", "host_mixed"):
         if adaptive:
             table.reset()
         otable = oracle.LengthTable(E) if adaptive else None
@@ -216,10 +220,23 @@ def test_pipeline_matches_oracle_config1(name, layout, olayout, bits, tsrc, otsr
             pipe.run(o, d, p, hits, pout)
             torch.cuda.synchronize()
             gh, gp = hits.cpu().numpy(), rr.u32_to_numpy(pout)
-        else:
-            gh = np.zeros((len(rays), 4), np.float32)
-            gp = np.zeros(len(rays), np.uint32)
+        elif entry == "host":
+            gh = np.zeros((n, 4), np.float32)
+            gp = np.zeros(n, np.uint32)
             pipe.run_host(rays.o_tmin, rays.d_tmax, rays.payload, gh, gp)
+        elif entry == "host_pinned":
+            ht = torch.zeros(n, 4).pin_memory()
+            pt = torch.zeros(n, dtype=torch.int32).pin_memory()
+            pipe.run_host(torch.from_numpy(rays.o_tmin).pin_memory(), torch.from_numpy(rays.d_tmax).pin_memory(),
+                          torch.from_numpy(rays.payload.view(np.int32)).pin_memory(), ht, pt)
+            gh, gp = ht.numpy().copy(), pt.numpy().view(np.uint32).copy()
+        else:
+            ht = torch.full((n + 3, 4), -7.0).pin_memory()
+            gp = np.zeros(n, np.uint32)
+            pipe.run_host(rays.o_tmin, rays.d_tmax, rays.payload, ht[1:n + 1], gp)
+            whole = ht.numpy()
+            assert (whole[0] == -7.0).all() and (whole[n + 1:] == -7.0).all(), "stores outside the hit range"
+            gh = whole[1:n + 1].copy()
         keys, perm, so, sd, sp, h, info = oracle_bounce(tris, rays, lo, hi, olayout, bits, otsrc, otable, obvh)
         assert np.array_equal(gp, sp)  # payload order == oracle permutation
         if entry == "device":
