@@ -337,16 +337,36 @@ rr_status rr_pipeline_run(rr_pipeline *p, const float *o_tmin, const float *d_tm
                           uint32_t *payload_out, void *stream);
 
 /*
- * rr_pipeline_run_host - host buffers (page-locked for full speed): copies the
- * rays to the device, runs the bounce, returns hits and payloads, and
- * synchronises `stream` (and the handle's side stream) before returning.
- * Payloads move on a side stream, overlapped with the key, sort and trace
- * kernels.  When hits_host is page-locked host memory (cudaHostAlloc or
+ * rr_pipeline_submit_host - one bounce on host buffers, enqueued without
+ * waiting.  Submissions alternate between two device staging slots, so the
+ * upload of one submission overlaps the kernels of the one before: rays and
+ * payloads go up on the handle's upload stream, the bounce runs on `stream`,
+ * sorted payloads come back on the handle's side stream while the trace runs.
+ * When hits_host is page-locked host memory (cudaHostAlloc or
  * cudaHostRegister) over its whole n * 16 bytes and 16-byte aligned, the trace
  * kernel stores the hits there directly, so their transfer overlaps the trace;
- * otherwise they are staged on the device and copied back.  Both forms give
- * the same bytes.  A hits_host whose first and last bytes are page-locked must
- * be page-locked in between (one allocation).
+ * otherwise they are staged on the device and copied back after it.  Both
+ * forms give the same bytes.  A hits_host whose first and last bytes are
+ * page-locked must be page-locked in between (one allocation).
+ *
+ * *ticket receives a number for rr_pipeline_wait (0 for n == 0).  Until that
+ * wait returns, the host buffers of the submission must stay allocated, its
+ * inputs unchanged and its outputs unread.  All submissions to one handle use
+ * the same `stream` (they share the handle's key, sort and sorted-ray
+ * buffers); with the adaptive estimate, each bounce sees the table updated by
+ * the submissions before it, as if they had run one after the other.
+ * Page-locked buffers give full link speed; pageable ones work, slower.
+ */
+rr_status rr_pipeline_submit_host(rr_pipeline *p, const float *o_tmin_host, const float *d_tmax_host,
+                                  const uint32_t *payload_host, uint32_t n, float *hits_host,
+                                  uint32_t *payload_out_host, void *stream, uint64_t *ticket);
+
+/* Blocks until submission `ticket` (and every submission before it on the
+ * handle) has written its hits and payloads to the host.  0 returns at once. */
+rr_status rr_pipeline_wait(rr_pipeline *p, uint64_t ticket);
+
+/*
+ * rr_pipeline_run_host - rr_pipeline_submit_host followed by rr_pipeline_wait.
  */
 rr_status rr_pipeline_run_host(rr_pipeline *p, const float *o_tmin_host, const float *d_tmax_host,
                                const uint32_t *payload_host, uint32_t n, float *hits_host,

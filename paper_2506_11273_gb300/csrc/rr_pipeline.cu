@@ -3,6 +3,18 @@
 // its estimate from the table (Section 3.1.6: accumulate after each trace).
 #include "rr_common.cuh"
 
+// Host-buffer submissions alternate between two staging slots, so the upload
+// of one submission overlaps the kernels of the one before it.
+struct HostSlot {
+    float *o_in = nullptr, *d_in = nullptr;  // uploaded rays
+    uint32_t *payload_in = nullptr, *payload_sorted = nullptr;
+    float *hits = nullptr;  // hits staged here when the caller's buffer is pageable
+    cudaEvent_t rays_up = nullptr, pay_up = nullptr;  // upload stream: rays, payloads arrived
+    cudaEvent_t consumed = nullptr;  // main stream: the reorder has read this slot's inputs
+    cudaEvent_t pay_down = nullptr;  // side stream: sorted payloads returned
+    cudaEvent_t done = nullptr;      // main stream: hits written (and returned)
+};
+
 struct rr_pipeline {
     const rr_bvh *bvh;
     uint32_t max_n;
@@ -14,14 +26,9 @@ struct rr_pipeline {
     void *keys;
     uint32_t *perm;
     float *o_sorted, *d_sorted;
-    uint32_t *payload_sorted;
-    float *o_in, *d_in;  // staging for rr_pipeline_run_host
-    uint32_t *payload_in;
-    float *hits;
-    // rr_pipeline_run_host moves the payloads on a side stream, overlapped
-    // with the key, sort and trace kernels of the main stream
-    cudaStream_t side = nullptr;
-    cudaEvent_t rays_in = nullptr, payload_in_done = nullptr, sorted = nullptr, payload_out_done = nullptr;
+    HostSlot slot[2];
+    cudaStream_t upload = nullptr, side = nullptr;
+    uint64_t submitted = 0;
 };
 
 namespace {
@@ -60,26 +67,21 @@ extern "C" rr_status rr_pipeline_create(const rr_bvh *bvh, uint32_t max_n, const
     if (st != RR_OK) return st;
     const size_t kb = params->bits > 32 ? 8 : 4;
     size_t off = 0;
-    const size_t o_ws = off;
-    off = up256(off + ws);
-    const size_t o_keys = off;
-    off = up256(off + kb * max_n);
-    const size_t o_perm = off;
-    off = up256(off + 4ull * max_n);
-    const size_t o_os = off;
-    off = up256(off + 16ull * max_n);
-    const size_t o_ds = off;
-    off = up256(off + 16ull * max_n);
-    const size_t o_ps = off;
-    off = up256(off + 4ull * max_n);
-    const size_t o_oi = off;
-    off = up256(off + 16ull * max_n);
-    const size_t o_di = off;
-    off = up256(off + 16ull * max_n);
-    const size_t o_pi = off;
-    off = up256(off + 4ull * max_n);
-    const size_t o_h = off;
-    off = up256(off + 16ull * max_n);
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = up256(off + bytes);
+        return at;
+    };
+    const size_t o_ws = take(ws), o_keys = take(kb * max_n), o_perm = take(4ull * max_n);
+    const size_t o_os = take(16ull * max_n), o_ds = take(16ull * max_n);
+    size_t o_slot[2][5];
+    for (auto &sl : o_slot) {
+        sl[0] = take(16ull * max_n);  // o_in
+        sl[1] = take(16ull * max_n);  // d_in
+        sl[2] = take(4ull * max_n);   // payload_in
+        sl[3] = take(4ull * max_n);   // payload_sorted
+        sl[4] = take(16ull * max_n);  // hits
+    }
     rr_pipeline *p = new rr_pipeline();
     cudaError_t e = cudaMalloc(&p->mem, off);
     if (e != cudaSuccess) {
@@ -97,17 +99,22 @@ extern "C" rr_status rr_pipeline_create(const rr_bvh *bvh, uint32_t max_n, const
     p->perm = reinterpret_cast<uint32_t *>(p->mem + o_perm);
     p->o_sorted = reinterpret_cast<float *>(p->mem + o_os);
     p->d_sorted = reinterpret_cast<float *>(p->mem + o_ds);
-    p->payload_sorted = reinterpret_cast<uint32_t *>(p->mem + o_ps);
-    p->o_in = reinterpret_cast<float *>(p->mem + o_oi);
-    p->d_in = reinterpret_cast<float *>(p->mem + o_di);
-    p->payload_in = reinterpret_cast<uint32_t *>(p->mem + o_pi);
-    p->hits = reinterpret_cast<float *>(p->mem + o_h);
-    e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
-    for (cudaEvent_t *ev : {&p->rays_in, &p->payload_in_done, &p->sorted, &p->payload_out_done})
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    for (int k = 0; k < 2; ++k) {
+        HostSlot &h = p->slot[k];
+        h.o_in = reinterpret_cast<float *>(p->mem + o_slot[k][0]);
+        h.d_in = reinterpret_cast<float *>(p->mem + o_slot[k][1]);
+        h.payload_in = reinterpret_cast<uint32_t *>(p->mem + o_slot[k][2]);
+        h.payload_sorted = reinterpret_cast<uint32_t *>(p->mem + o_slot[k][3]);
+        h.hits = reinterpret_cast<float *>(p->mem + o_slot[k][4]);
+    }
+    e = cudaStreamCreateWithFlags(&p->upload, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+    for (HostSlot &h : p->slot)
+        for (cudaEvent_t *ev : {&h.rays_up, &h.pay_up, &h.consumed, &h.pay_down, &h.done})
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         rr_pipeline_destroy(p);
-        return fail_cuda(e, "rr_pipeline_create: stream or events");
+        return fail_cuda(e, "rr_pipeline_create: streams or events");
     }
     *out = p;
     return RR_OK;
@@ -115,8 +122,13 @@ extern "C" rr_status rr_pipeline_create(const rr_bvh *bvh, uint32_t max_n, const
 
 extern "C" rr_status rr_pipeline_destroy(rr_pipeline *p) {
     if (!p) return RR_OK;
-    for (cudaEvent_t ev : {p->rays_in, p->payload_in_done, p->sorted, p->payload_out_done})
-        if (ev) cudaEventDestroy(ev);
+    for (HostSlot &h : p->slot)
+        for (cudaEvent_t ev : {h.rays_up, h.pay_up, h.consumed, h.pay_down, h.done})
+            if (ev) cudaEventSynchronize(ev);
+    for (HostSlot &h : p->slot)
+        for (cudaEvent_t ev : {h.rays_up, h.pay_up, h.consumed, h.pay_down, h.done})
+            if (ev) cudaEventDestroy(ev);
+    if (p->upload) cudaStreamDestroy(p->upload);
     if (p->side) cudaStreamDestroy(p->side);
     cudaFree(p->mem);
     delete p;
@@ -125,26 +137,37 @@ extern "C" rr_status rr_pipeline_destroy(rr_pipeline *p) {
 
 namespace {
 
-// The bounce on device buffers.  When `payload_ready` is set, the stream waits
-// for it before the reorder (the only step that reads payloads); when `sorted`
-// is set, it is recorded after the reorder.
+// Events that order one host submission's bounce with its uploads and
+// downloads; all null for rr_pipeline_run.
+struct BounceSync {
+    cudaEvent_t rays_ready = nullptr;    // wait before the keys
+    cudaEvent_t payload_ready = nullptr; // wait before the reorder
+    cudaEvent_t payload_free = nullptr;  // wait before the reorder (previous reader of payload_out)
+    cudaEvent_t consumed = nullptr;      // record after the reorder
+};
+
+rr_status wait_on(cudaStream_t s, cudaEvent_t ev) {
+    if (!ev) return RR_OK;
+    const cudaError_t e = cudaStreamWaitEvent(s, ev, 0);
+    return e == cudaSuccess ? RR_OK : fail_cuda(e, "rr_pipeline: stream wait");
+}
+
+// The bounce on device buffers, enqueued on `stream`.
 rr_status run_bounce(rr_pipeline *p, const float *o_tmin, const float *d_tmax, const uint32_t *payload_in,
-                     uint32_t n, float *hits_out, uint32_t *payload_out, void *stream, cudaEvent_t payload_ready,
-                     cudaEvent_t sorted) {
-    rr_status st = rr_compute_keys(o_tmin, d_tmax, n, &p->params, p->keys, stream);
-    if (st != RR_OK) return st;
-    st = rr_sort(p->keys, nullptr, p->perm, n, p->params.bits, p->radix_bits, p->workspace, p->ws_bytes, stream);
-    if (st != RR_OK) return st;
+                     uint32_t n, float *hits_out, uint32_t *payload_out, void *stream, const BounceSync &sync) {
     cudaStream_t s = as_stream(stream);
-    if (payload_ready) {
-        const cudaError_t e = cudaStreamWaitEvent(s, payload_ready, 0);
-        if (e != cudaSuccess) return fail_cuda(e, "rr_pipeline_run_host: wait for payloads");
-    }
-    st = rr_permute(o_tmin, d_tmax, payload_in, p->perm, n, p->o_sorted, p->d_sorted, payload_out, stream);
+    rr_status st = wait_on(s, sync.rays_ready);
+    if (st == RR_OK) st = rr_compute_keys(o_tmin, d_tmax, n, &p->params, p->keys, stream);
+    if (st == RR_OK)
+        st = rr_sort(p->keys, nullptr, p->perm, n, p->params.bits, p->radix_bits, p->workspace, p->ws_bytes, stream);
+    if (st == RR_OK) st = wait_on(s, sync.payload_ready);
+    if (st == RR_OK) st = wait_on(s, sync.payload_free);
+    if (st == RR_OK)
+        st = rr_permute(o_tmin, d_tmax, payload_in, p->perm, n, p->o_sorted, p->d_sorted, payload_out, stream);
     if (st != RR_OK) return st;
-    if (sorted) {
-        const cudaError_t e = cudaEventRecord(sorted, s);
-        if (e != cudaSuccess) return fail_cuda(e, "rr_pipeline_run_host: record");
+    if (sync.consumed) {
+        const cudaError_t e = cudaEventRecord(sync.consumed, s);
+        if (e != cudaSuccess) return fail_cuda(e, "rr_pipeline: record");
     }
     if (p->params.layout == RR_KEY_TWO_POINT && p->params.t_source == RR_T_ADAPTIVE)
         return rr_trace_accumulate(p->bvh, p->o_sorted, p->d_sorted, n, hits_out,
@@ -162,56 +185,88 @@ extern "C" rr_status rr_pipeline_run(rr_pipeline *p, const float *o_tmin, const 
     if (n == 0) return RR_OK;
     if ((payload_in == nullptr) != (payload_out == nullptr))
         return fail(RR_ERR_INVALID_ARG, "rr_pipeline_run: payload_in and payload_out must both be set or both NULL");
-    return run_bounce(p, o_tmin, d_tmax, payload_in, n, hits_out, payload_out, stream, nullptr, nullptr);
+    return run_bounce(p, o_tmin, d_tmax, payload_in, n, hits_out, payload_out, stream, BounceSync{});
 }
 
-// Host buffers.  The rays go up first (the keys need them); the payloads go up
-// on the side stream while the keys and the sort run, and come back on it
-// while the trace runs.  Hits in page-locked host memory are stored there by
-// the trace kernel itself, so their transfer overlaps the trace; otherwise
-// they are staged on the device and copied back after it.
-extern "C" rr_status rr_pipeline_run_host(rr_pipeline *p, const float *o_host, const float *d_host,
-                                          const uint32_t *payload_host, uint32_t n, float *hits_host,
-                                          uint32_t *payload_out_host, void *stream) {
-    if (!p) return fail(RR_ERR_INVALID_ARG, "rr_pipeline_run_host: NULL pipeline");
-    if (n > p->max_n) return fail(RR_ERR_INVALID_ARG, "rr_pipeline_run_host: n exceeds max_n");
+// Host buffers, without waiting.  Submission k uses staging slot k mod 2: its
+// rays and payloads go up on the upload stream (after submission k-2 has
+// read the slot), the bounce runs on `stream`, the sorted payloads come back
+// on the side stream while the trace runs, and hits in page-locked host
+// memory are stored there by the trace kernel itself (otherwise staged on the
+// device and copied back on `stream` after it).
+extern "C" rr_status rr_pipeline_submit_host(rr_pipeline *p, const float *o_host, const float *d_host,
+                                             const uint32_t *payload_host, uint32_t n, float *hits_host,
+                                             uint32_t *payload_out_host, void *stream, uint64_t *ticket) {
+    if (!p) return fail(RR_ERR_INVALID_ARG, "rr_pipeline_submit_host: NULL pipeline");
+    if (ticket) *ticket = 0;
+    if (n > p->max_n) return fail(RR_ERR_INVALID_ARG, "rr_pipeline_submit_host: n exceeds max_n");
     if (n == 0) return RR_OK;
-    if (!o_host || !d_host || !hits_host) return fail(RR_ERR_INVALID_ARG, "rr_pipeline_run_host: NULL buffer");
+    if (!o_host || !d_host || !hits_host) return fail(RR_ERR_INVALID_ARG, "rr_pipeline_submit_host: NULL buffer");
     if ((payload_host == nullptr) != (payload_out_host == nullptr))
-        return fail(RR_ERR_INVALID_ARG, "rr_pipeline_run_host: payload in/out must both be set or both NULL");
+        return fail(RR_ERR_INVALID_ARG, "rr_pipeline_submit_host: payload in/out must both be set or both NULL");
     cudaStream_t s = as_stream(stream);
+    const uint64_t k = p->submitted++;
+    HostSlot &h = p->slot[k & 1];
     const bool pay = payload_host != nullptr;
     float *hits_direct = static_cast<float *>(mapped_host(hits_host, 16ull * n));
     if (hits_direct && !aligned(hits_direct, 16)) hits_direct = nullptr;
-    cudaError_t e = cudaMemcpyAsync(p->o_in, o_host, 16ull * n, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_in, d_host, 16ull * n, cudaMemcpyHostToDevice, s);
+    // uploads: after the reorder of submission k-2 has read this slot
+    cudaError_t e = cudaStreamWaitEvent(p->upload, h.consumed, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.o_in, o_host, 16ull * n, cudaMemcpyHostToDevice, p->upload);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.d_in, d_host, 16ull * n, cudaMemcpyHostToDevice, p->upload);
+    if (e == cudaSuccess) e = cudaEventRecord(h.rays_up, p->upload);
     if (pay) {
-        if (e == cudaSuccess) e = cudaEventRecord(p->rays_in, s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->rays_in, 0);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(p->payload_in, payload_host, 4ull * n, cudaMemcpyHostToDevice, p->side);
-        if (e == cudaSuccess) e = cudaEventRecord(p->payload_in_done, p->side);
+            e = cudaMemcpyAsync(h.payload_in, payload_host, 4ull * n, cudaMemcpyHostToDevice, p->upload);
+        if (e == cudaSuccess) e = cudaEventRecord(h.pay_up, p->upload);
     }
-    if (e != cudaSuccess) return fail_cuda(e, "rr_pipeline_run_host: upload");
-    rr_status st = run_bounce(p, p->o_in, p->d_in, pay ? p->payload_in : nullptr, n, hits_direct ? hits_direct : p->hits,
-                              pay ? p->payload_sorted : nullptr, stream, pay ? p->payload_in_done : nullptr,
-                              pay ? p->sorted : nullptr);
+    if (e != cudaSuccess) return fail_cuda(e, "rr_pipeline_submit_host: upload");
+    BounceSync sync;
+    sync.rays_ready = h.rays_up;
+    sync.payload_ready = pay ? h.pay_up : nullptr;
+    sync.payload_free = pay ? h.pay_down : nullptr;
+    sync.consumed = h.consumed;
+    rr_status st = run_bounce(p, h.o_in, h.d_in, pay ? h.payload_in : nullptr, n, hits_direct ? hits_direct : h.hits,
+                              pay ? h.payload_sorted : nullptr, stream, sync);
+    if (st != RR_OK) return st;
+    if (pay) {
+        e = cudaStreamWaitEvent(p->side, h.consumed, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(payload_out_host, h.payload_sorted, 4ull * n, cudaMemcpyDeviceToHost, p->side);
+        if (e == cudaSuccess) e = cudaEventRecord(h.pay_down, p->side);
+    }
+    if (e == cudaSuccess && !hits_direct) e = cudaMemcpyAsync(hits_host, h.hits, 16ull * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(h.done, s);
+    if (e != cudaSuccess) return fail_cuda(e, "rr_pipeline_submit_host: download");
+    if (ticket) *ticket = k + 1;
+    return RR_OK;
+}
+
+extern "C" rr_status rr_pipeline_wait(rr_pipeline *p, uint64_t ticket) {
+    if (!p) return fail(RR_ERR_INVALID_ARG, "rr_pipeline_wait: NULL pipeline");
+    if (ticket == 0) return RR_OK;  // an empty submission
+    if (ticket > p->submitted) return fail(RR_ERR_INVALID_ARG, "rr_pipeline_wait: ticket was never issued");
+    // a slot's events are re-recorded by later submissions; those complete
+    // after this one, so waiting on them is never too early
+    HostSlot &h = p->slot[(ticket - 1) & 1];
+    cudaError_t e = cudaEventSynchronize(h.done);
+    if (e == cudaSuccess) e = cudaEventSynchronize(h.pay_down);
+    if (e != cudaSuccess) return fail_cuda(e, "rr_pipeline_wait");
+    return RR_OK;
+}
+
+extern "C" rr_status rr_pipeline_run_host(rr_pipeline *p, const float *o_host, const float *d_host,
+                                          const uint32_t *payload_host, uint32_t n, float *hits_host,
+                                          uint32_t *payload_out_host, void *stream) {
+    uint64_t ticket = 0;
+    rr_status st = rr_pipeline_submit_host(p, o_host, d_host, payload_host, n, hits_host, payload_out_host, stream,
+                                           &ticket);
     if (st != RR_OK) {
-        cudaStreamSynchronize(p->side);
+        if (p) {
+            cudaStreamSynchronize(p->upload);
+            cudaStreamSynchronize(p->side);
+        }
         return st;
     }
-    if (pay) {
-        e = cudaStreamWaitEvent(p->side, p->sorted, 0);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(payload_out_host, p->payload_sorted, 4ull * n, cudaMemcpyDeviceToHost, p->side);
-        if (e == cudaSuccess) e = cudaEventRecord(p->payload_out_done, p->side);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->payload_out_done, 0);
-    }
-    if (e == cudaSuccess && !hits_direct) e = cudaMemcpyAsync(hits_host, p->hits, 16ull * n, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-        cudaStreamSynchronize(p->side);
-        return fail_cuda(e, "rr_pipeline_run_host: download");
-    }
-    return RR_OK;
+    return rr_pipeline_wait(p, ticket);
 }

@@ -46,7 +46,8 @@ EXPORTS = [
     "rr_bvh_destroy", "rr_bvh_get_info", "rr_trace", "rr_trace_accumulate", "rr_length_table_create",
     "rr_length_table_reset", "rr_length_table_accumulate", "rr_length_table_read",
     "rr_length_table_write", "rr_length_table_destroy", "rr_pipeline_create",
-    "rr_pipeline_destroy", "rr_pipeline_run", "rr_pipeline_run_host", "rr_device_error",
+    "rr_pipeline_destroy", "rr_pipeline_run", "rr_pipeline_run_host", "rr_pipeline_submit_host",
+    "rr_pipeline_wait", "rr_device_error",
     "rr_status_string", "rr_last_error_message", "rr_kernel_launch_count", "rr_sort_noalloc",
     "rr_coherence_capsule", "rr_trace_ex", "rr_sort_segments", "rr_batch_create", "rr_batch_destroy",
     "rr_batch_info", "rr_batch_run", "rr_batch_run_loop", "rr_batch_tune", "rr_server_create",
@@ -134,6 +135,8 @@ def lib():
             L.rr_pipeline_destroy.argtypes = [vp]
             L.rr_pipeline_run.argtypes = [vp, vp, vp, vp, u32, vp, vp, vp]
             L.rr_pipeline_run_host.argtypes = [vp, vp, vp, vp, u32, vp, vp, vp]
+            L.rr_pipeline_submit_host.argtypes = [vp, vp, vp, vp, u32, vp, vp, vp, C.POINTER(C.c_uint64)]
+            L.rr_pipeline_wait.argtypes = [vp, C.c_uint64]
             L.rr_sort_segments.argtypes = [vp, vp, vp, u32, u32, u32, vp]
             L.rr_trace_ex.argtypes = [vp, vp, vp, vp, u32, vp, u32, vp, vp]
             L.rr_batch_create.argtypes = [C.POINTER(Wavefront), u32, u32, u32, C.c_float, C.POINTER(vp)]
@@ -402,6 +405,20 @@ class Pipeline:
         _check(lib().rr_pipeline_run_host(self.handle, _hptr(o_tmin), _hptr(d_tmax),
                                           _hptr(payload_in), n, _hptr(hits_out), _hptr(payload_out),
                                           _stream(stream)), "rr_pipeline_run_host")
+
+    def submit_host(self, o_tmin, d_tmax, payload_in, hits_out, payload_out, n: int | None = None,
+                    stream=None) -> int:
+        """Enqueues one bounce on host buffers and returns its ticket; the
+        buffers belong to the submission until wait(ticket) returns."""
+        n = o_tmin.shape[0] if n is None else n
+        t = C.c_uint64(0)
+        _check(lib().rr_pipeline_submit_host(self.handle, _hptr(o_tmin), _hptr(d_tmax), _hptr(payload_in), n,
+                                             _hptr(hits_out), _hptr(payload_out), _stream(stream), C.byref(t)),
+               "rr_pipeline_submit_host")
+        return t.value
+
+    def wait(self, ticket: int):
+        _check(lib().rr_pipeline_wait(self.handle, ticket), "rr_pipeline_wait")
 
     def close(self):
         if getattr(self, "handle", None):

@@ -250,6 +250,60 @@ def test_pipeline_matches_oracle_config1(name, layout, olayout, bits, tsrc, otsr
     pipe.close()
 
 
+def test_pipeline_submissions_in_flight_match_one_after_another():
+    """Host submissions with two in flight (the upload of one overlapping the
+    kernels of the one before) give the bytes of the same bounces run one after
+    the other, with the adaptive table carried from bounce to bounce.  Page-locked
+    and pageable output buffers, uneven sizes, and a ticket waited on twice."""
+    tris = W.scene_box_soup(seed=2)
+    lo, hi = W.scene_aabb(tris)
+    bvh = rr.BVH(tris)
+    sizes = [65536, 40001, 65536, 777]
+    waves = [W.rays_box_soup(tris, n=m, seed=20 + j) for j, m in enumerate(sizes)]
+    table = rr.LengthTable(lo, hi)
+    params = rr.key_params(rr.RR_KEY_TWO_POINT, 64, lo, hi, t_source=rr.RR_T_ADAPTIVE, table=table)
+    pipe = rr.Pipeline(bvh, max(sizes), params, radix_bits=8)
+
+    def outputs(m, pinned):
+        if pinned:
+            return torch.zeros(m, 4).pin_memory(), torch.zeros(m, dtype=torch.int32).pin_memory()
+        return np.zeros((m, 4), np.float32), np.zeros(m, np.int32)
+
+    def as_np(x):
+        return (x.numpy() if isinstance(x, torch.Tensor) else x).copy()
+
+    table.reset()
+    ref = []
+    for r in waves:
+        h, q = outputs(len(r), False)
+        pipe.run_host(r.o_tmin, r.d_tmax, r.payload, h, q)
+        ref.append((h.copy(), q.copy()))
+    ref_table = table.read()
+
+    table.reset()
+    inputs = [(torch.from_numpy(r.o_tmin).pin_memory(), torch.from_numpy(r.d_tmax).pin_memory(),
+               torch.from_numpy(r.payload.view(np.int32)).pin_memory()) for r in waves]
+    outs = [outputs(len(r), pinned=(j != 1)) for j, r in enumerate(waves)]
+    tickets = []
+    for j, (o, d, p) in enumerate(inputs):
+        tickets.append(pipe.submit_host(o, d, p, *outs[j]))
+        if j >= 1:
+            pipe.wait(tickets[j - 1])
+    pipe.wait(tickets[-1])
+    pipe.wait(tickets[0])  # long done: returns at once
+    for j in range(len(waves)):
+        h, q = as_np(outs[j][0]), as_np(outs[j][1])
+        assert np.array_equal(h.view(np.uint32), ref[j][0].view(np.uint32)), j
+        assert np.array_equal(q, ref[j][1]), j
+    got_table = table.read()
+    assert all(np.array_equal(a, b) for a, b in zip(got_table, ref_table))
+    assert pipe.submit_host(waves[0].o_tmin, waves[0].d_tmax, None, np.zeros((0, 4), np.float32), None, n=0) == 0
+    with pytest.raises(rr.RRError):
+        pipe.wait(10 ** 6)
+    assert rr.rr_device_error() == 0
+    pipe.close()
+
+
 def test_pipeline_rejects_bad_arguments():
     tris = W.scene_box_soup(seed=1, n_random=64)
     lo, hi = W.scene_aabb(tris)
