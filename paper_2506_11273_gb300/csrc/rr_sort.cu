@@ -20,7 +20,6 @@ constexpr unsigned long long kReady = 1ull << 63;
 constexpr uint32_t kSpinLimit = 1u << 20;   // bounded wait on a predecessor's word
 constexpr int kSortBlock = 256;
 constexpr int kSortWarps = kSortBlock / 32;
-constexpr uint32_t kHistMaxBlocks = 512;    // blocks of the counting pass
 
 __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p) {
     unsigned long long v;
@@ -558,8 +557,12 @@ static cudaError_t enqueue_sort(const SortPlan &pl, const K *keys_in, K *keys_ou
     if (e != cudaSuccess) return e;
     const size_t zero_count = (size_t)pl.passes * pl.tiles * pl.radix / 2;  // uint4 = two words
     const uint32_t per_block = kSortBlock * 4u;
+    // counting-pass grid: two blocks per SM up to ~2M keys, then one block per
+    // 8 rounds of keys up to eight per SM (more blocks in flight hide the
+    // loads; each block adds its counters to the global histogram once)
+    const uint32_t sms = (uint32_t)sm_count;
     const uint32_t hist_blocks = std::max(
-        1u, std::min({(n + per_block - 1) / per_block, 2u * (uint32_t)sm_count, kHistMaxBlocks}));
+        1u, std::min({(n + per_block - 1) / per_block, std::max(2u * sms, n / (8u * per_block)), 8u * sms}));
     sort_histogram_kernel<K, RBITS><<<hist_blocks, kSortBlock, 0, s>>>(
         keys_in, n, bits, pl.passes, hist, reinterpret_cast<uint4 *>(lookback), zero_count, counters, zero_err);
     const K *kin = keys_in;
