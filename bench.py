@@ -892,6 +892,25 @@ def bench_serving(args, dev, slots: int = 4, max_batch_rays: int = 1 << 23, frac
     setup_s = time.time() - t0
     hits_sink = torch.empty(hi_n, 4).pin_memory()  # results are written here and not read
 
+    def link_gbs():
+        # host-link copy rates of the request pools and the result buffer
+        o = pools[(0, "diffuse")][0]
+        dst = torch.empty(o.shape, dtype=o.dtype, device=dev)
+        hs = torch.empty(hits_sink.shape, dtype=hits_sink.dtype, device=dev)
+        rates = []
+        for src, dd, h2d in ((o, dst, True), (hits_sink, hs, False)):
+            best = 1e9
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                (dd.copy_(src, non_blocking=True) if h2d else src.copy_(dd, non_blocking=True))
+                torch.cuda.synchronize()
+                best = min(best, time.perf_counter() - t1)
+            rates.append(round(src.numel() * src.element_size() / best / 1e9, 1))
+        del dst, hs
+        return rates
+    link_before = link_gbs()
+
     def run_load(rate_rps, duration_s, seed):
         rng = np.random.default_rng(seed)
         n_req = max(8, int(rate_rps * duration_s))
@@ -911,10 +930,12 @@ def bench_serving(args, dev, slots: int = 4, max_batch_rays: int = 1 << 23, frac
                 time.sleep(min(dt, 0.0005))
             o, d = pools[(int(which[k]), str(kinds[k]))]
             tickets.append((srv.submit(int(which[k]), o, d, hits_sink, n=int(sizes[k])), int(sizes[k])))
-        lat, rays, first, last = [], 0, None, None
+        lat, queued, service, rays, first, last = [], [], [], 0, None, None
         for t, n in tickets:
             tm = srv.wait(t)
             lat.append((tm["done_ns"] - tm["submit_ns"]) * 1e-6)
+            queued.append((tm["start_ns"] - tm["submit_ns"]) * 1e-6)
+            service.append((tm["done_ns"] - tm["start_ns"]) * 1e-6)
             rays += n
             first = tm["submit_ns"] if first is None else min(first, tm["submit_ns"])
             last = tm["done_ns"] if last is None else max(last, tm["done_ns"])
@@ -923,6 +944,8 @@ def bench_serving(args, dev, slots: int = 4, max_batch_rays: int = 1 << 23, frac
         return {"offered_rps": round(rate_rps, 1), "offered_mrays": round(rate_rps * float(np.mean(sizes)) / 1e6, 1),
                 "requests": n_req, "p50_ms": round(float(np.percentile(lat, 50)), 3),
                 "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(lat.mean()), 3),
+                "queued_p50_p99_ms": [round(float(np.percentile(queued, q)), 3) for q in (50, 99)],
+                "in_batch_p50_p99_ms": [round(float(np.percentile(service, q)), 3) for q in (50, 99)],
                 "throughput_mrays": round(rays / span / 1e6, 1)}
 
     # capacity: bursts of 256 requests submitted at once (the better of two),
@@ -932,9 +955,10 @@ def bench_serving(args, dev, slots: int = 4, max_batch_rays: int = 1 << 23, frac
     cap_mrays = max(run_load(1e6, 256 / 1e6, seed=s)["throughput_mrays"] for s in (1, 3))
     cap_rps = cap_mrays * 1e6 / mean_n
     loads = []
-    for frac in fractions:
-        loads.append(dict(run_load(frac * cap_rps, 1.5 if not small else 0.5, seed=int(frac * 100)),
-                          load_frac=frac))
+    with ClockSampler(dev.index or 0) as clk:
+        for frac in fractions:
+            loads.append(dict(run_load(frac * cap_rps, 1.5 if not small else 0.5, seed=int(frac * 100)),
+                              load_frac=frac))
     st = srv.stats()
     srv.close()
     return {"workload": "Poisson arrivals of log-uniform %d-%d-ray requests (60%% diffuse, 40%% glossy) over 8 "
@@ -943,6 +967,8 @@ def bench_serving(args, dev, slots: int = 4, max_batch_rays: int = 1 << 23, frac
                                                    SERVE_BUDGET >> 30, slots, max(max_batch_rays, hi_n)),
             "capacity_mrays": cap_mrays, "loads": loads, "setup_s": round(setup_s, 1),
             "batches": st["batches"], "max_batch_requests": st["max_batch_requests"],
+            "clocks": clk.summary(),
+            "pool_h2d_result_d2h_gbs": link_before,
             "peak_reserved_gb": round(st["peak_reserved_bytes"] / 2**30, 2)}
 
 
