@@ -45,6 +45,8 @@
  *    A miss is t = +inf, u = v = 0, id = 0xFFFFFFFF.  Hits are written in the
  *    order of the rays that were traced.
  *  - Keys are uint32 when bits <= 32 and uint64 when 32 < bits <= 64.
+ *  - A handle is used by one host thread at a time; rr_server's calls may come
+ *    from any thread.
  */
 #ifndef RR_H
 #define RR_H
