@@ -169,7 +169,12 @@ rr_status rr_sort_workspace_size(uint32_t n, uint32_t bits, uint32_t radix_bits,
  * and perm_out must not overlap.  workspace: device, at least
  * rr_sort_workspace_size() bytes, 256-byte aligned, owned by the caller and
  * free again once the work on `stream` has completed.  n < 2^30.
- * One histogram pass plus ceil(bits / radix_bits) onesweep passes are enqueued.
+ * One histogram pass plus ceil(bits / radix_bits) onesweep passes are enqueued;
+ * the passes use programmatic dependent launch, and the last one lets the next
+ * kernel of `stream` start early: a caller's kernel launched there with
+ * cudaLaunchAttributeProgrammaticStreamSerialization must call
+ * cudaGridDependencySynchronize() before it reads the sort's outputs (kernels
+ * launched without that attribute wait for the sort as usual).
  */
 rr_status rr_sort(const void *keys_in, void *keys_out, uint32_t *perm_out, uint32_t n,
                   uint32_t bits, uint32_t radix_bits, void *workspace, size_t workspace_bytes,
