@@ -204,8 +204,9 @@ rr_status rr_sort_segments(const void *keys_in, void *keys_out, uint32_t *perm_o
  * device array of RR_SORT_NOALLOC_SCRATCH_BYTES (26 MiB) inside librr.so, and
  * every GPU that loads the library holds that array until the process exits.
  *
- * Arguments and results are those of rr_sort without the workspace: perm_out
- * receives the stable order, keys_out (may be NULL) the sorted keys.  n may be
+ * Arguments, results and launches are those of rr_sort without the workspace
+ * (including its programmatic dependent launch): perm_out receives the stable
+ * order, keys_out (may be NULL) the sorted keys.  n may be
  * at most RR_SORT_NOALLOC_MAX_N (2^20 keys); a larger n returns
  * RR_ERR_TOO_LARGE and enqueues nothing.  Other bad arguments return
  * RR_ERR_INVALID_ARG.  Errors are reported by the returned status only; this
