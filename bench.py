@@ -391,7 +391,13 @@ def run_ours(args):
         variants = {}
         kv = max(3, args.steps // 2)
         params_costa32 = rr.key_params(rr.RR_KEY_COSTA, 32, lo, hi)
+        params_costa24 = rr.key_params(rr.RR_KEY_COSTA, 24, lo, hi)
+        params_costa16 = rr.key_params(rr.RR_KEY_COSTA, 16, lo, hi)
         for name, kw in [("global64_indirect", dict(params=params_tp, accumulate=True, reorder="indirect")),
+                         ("costa24_indirect", dict(params=params_costa24, accumulate=False, bits=24,
+                                                   reorder="indirect")),
+                         ("costa16_indirect", dict(params=params_costa16, accumulate=False, bits=16,
+                                                   reorder="indirect")),
                          ("costa32_gather", dict(params=params_costa32, accumulate=False, bits=32)),
                          ("costa32_indirect", dict(params=params_costa32, accumulate=False, bits=32,
                                                    reorder="indirect")),
