@@ -703,19 +703,21 @@ def run_sweep(args):
                          "sort_frac_hbm": round(sort_bytes / (float(ph[1]) * 1e-3) / 1e9 / hbm, 3)})
             del ws
         del keys
-    # the direction-first Costa key (32 bits) with the gather and with indirect access
+    # the direction-first Costa key (32 bits with the gather and with indirect
+    # access; 24 bits with indirect access)
     keys32 = torch.empty(n, dtype=torch.int32, device=dev)
     ws32 = rr.sort_workspace(n, 32, 8, dev)
-    params_c = rr.key_params(rr.RR_KEY_COSTA, 32, lo, hi)
     extra_rows = {}
-    for reorder in ("gather", "indirect"):
+    for cbits, reorder in ((32, "gather"), (32, "indirect"), (24, "indirect")):
+        params_c = rr.key_params(rr.RR_KEY_COSTA, cbits, lo, hi)
+
         def step_c(evs):
             if evs:
                 evs[0].record(stream)
             rr.rr_compute_keys(o, d, params_c, keys32)
             if evs:
                 evs[1].record(stream)
-            rr.rr_sort(keys32, None, perm, n, 32, 8, ws32)
+            rr.rr_sort(keys32, None, perm, n, cbits, 8, ws32)
             if evs:
                 evs[2].record(stream)
             if reorder == "gather":
@@ -730,7 +732,7 @@ def run_sweep(args):
             if evs:
                 evs[4].record(stream)
         ph = timed(step_c, 5)
-        extra_rows["costa32_" + reorder] = {
+        extra_rows["costa%d_%s" % (cbits, reorder)] = {
             "key_ms": round(float(ph[0]), 4), "sort_ms": round(float(ph[1]), 4), "gather_ms": round(float(ph[2]), 4),
             "trace_ms": round(float(ph[3]), 4), "sorted_e2e_mrays": round(n / (float(ph.sum()) * 1e-3) / 1e6, 1)}
     if rr.rr_device_error() != 0:
