@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--bounce", type=int, default=3)
     ap.add_argument("--small", action="store_true", help="tiny scene and wavefront (for profiling runs)")
-    ap.add_argument("--no-extra", action="store_true", help="skip the per-bounce and e2e sweeps")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other keys, reorder variants, shadow rays and per-bounce sweep (the e2e run stays)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-execution measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--sweep", action="store_true",
