@@ -139,6 +139,45 @@ def test_trace_known_barycentric_points_and_two_sided():
             assert abs(t - s) < 1e-9 and abs(uu - u) < 1e-9 and abs(vv - v) < 1e-9
 
 
+@pytest.mark.parametrize("edge", ["u", "v", "w"])
+def test_ray_triangle_uv_signed_margin_at_each_edge(edge):
+    """or_ray_triangle_uv, the helper that decides which hit disagreements are
+    edge cases: rays aimed at points just inside and just outside each edge
+    of a triangle (tiny steps across the edge) return the barycentrics of the
+    target point and its distance, in closed form, from both sides, and the
+    signed margin min(u, v, 1-u-v) changes sign exactly across the edge."""
+    tri = np.array([0.25, 0.5, 0.125, 1.25, 0.75, 0.375, 0.5, 1.5, -0.25], np.float32)
+    v0, v1, v2 = (tri[0:3].astype(np.float64), tri[3:6].astype(np.float64), tri[6:9].astype(np.float64))
+    e1, e2 = v1 - v0, v2 - v0
+    rng = np.random.default_rng({"u": 1, "v": 2, "w": 3}[edge])
+    for step in (1e-3, 1e-6, -1e-6, -1e-3):  # > 0: inside by `step`, < 0: outside
+        s = rng.uniform(0.2, 0.8)
+        if edge == "u":      # edge v0-v2: u = step
+            u, v = step, s * (1 - step)
+        elif edge == "v":    # edge v0-v1: v = step
+            u, v = s * (1 - step), step
+        else:                # edge v1-v2: 1 - u - v = step
+            u = s * (1 - step)
+            v = 1 - step - u
+        p = v0 + u * e1 + v * e2
+        for sign in (1.0, -1.0):
+            d = sign * np.array([0.3, -0.2, 1.0]) + 0.1 * rng.standard_normal(3)
+            t_true = rng.uniform(0.5, 3.0)
+            o = p - t_true * d
+            ok, t, uu, vv = oracle.ray_plane_barycentrics(o, d, tri)
+            assert ok
+            assert abs(t - t_true) <= 1e-12 * t_true
+            assert abs(uu - u) <= 1e-12 and abs(vv - v) <= 1e-12
+            margin = min(uu, vv, 1.0 - uu - vv)
+            assert abs(margin - step) <= 1e-12
+            assert (margin > 0) == (step > 0)
+    # a ray in the triangle's plane has no solution
+    n = np.cross(e1, e2)
+    d_par = np.cross(n, e1)
+    ok, _, _, _ = oracle.ray_plane_barycentrics(v0 - d_par, d_par, tri)
+    assert not ok
+
+
 def test_trace_open_interval_and_parallel_miss():
     tri = np.array([0, 0, 0, 1, 0, 0, 0, 1, 0], np.float32)  # z = 0 plane
     o_tmin = np.array([[0.25, 0.25, 1.0, 0.0]], np.float32)
