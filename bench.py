@@ -23,7 +23,6 @@ import argparse
 import hashlib
 import json
 import os
-import re
 import subprocess
 import sys
 import time
@@ -43,10 +42,14 @@ BYTES_SORT = 8 + (KEY_BITS // RADIX_BITS) * 2 * (8 + 4) - 4   # 196 for 64-bit k
 BYTES_GATHER = 4 + 36 + 36
 BYTES_TRACE = 32 + 16
 BYTES_ACCUM = 32 + 16
-TRACE_PROFILE = os.path.join("profiles", "trace_kernel_config2_bounce3.md")
 TRACE_SOURCES = ["paper_2506_11273_gb300/csrc/rr_trace.cu", "paper_2506_11273_gb300/csrc/rr_trace.h",
                  "paper_2506_11273_gb300/csrc/rr_common.cuh", "paper_2506_11273_gb300/csrc/rr_bvh.cpp",
                  "paper_2506_11273_gb300/csrc/rr_keymath.cuh", "paper_2506_11273_gb300/csrc/rr_batch.cuh"]
+# One ncu capture of the fused trace kernel on this workload (bounce-3 wavefront,
+# sorted rays): DRAM bytes read + written and warp instructions per launch, valid
+# only while the trace sources hash to `sources` (sha256 of TRACE_SOURCES, first
+# 16 hex digits); otherwise traffic is reported as null.
+TRACE_NCU = {"sources": None, "dram_bytes": None, "warp_instructions": None}
 # issue-slot peak: 4 warp instructions per cycle per SM (one per scheduler) x 152 SMs
 SMS, ISSUE_PER_SM_CYCLE, MAX_SM_MHZ = 152, 4, 2070.0
 
@@ -101,24 +104,19 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def measured_trace_counts():
-    """(DRAM bytes, warp instructions) per trace launch from the committed ncu
-    summary, or (None, None) when the trace kernel's sources have changed since
-    that capture."""
+def trace_ncu_counts():
+    """(DRAM bytes, warp instructions) per trace launch from the recorded ncu
+    capture, or (None, None) when the trace kernel's sources have changed since."""
+    h = hashlib.sha256()
     try:
-        text = open(os.path.join(ROOT, TRACE_PROFILE)).read()
-        h = hashlib.sha256()
         for src in TRACE_SOURCES:
             with open(os.path.join(ROOT, src), "rb") as f:
                 h.update(f.read())
     except OSError:
         return None, None
-    m_bytes = re.search(r"traffic_bytes = (\d+)", text)
-    m_inst = re.search(r"inst_executed = (\d+)", text)
-    m_hash = re.search(r"traffic_source_sha256_16: ([0-9a-f]+)", text)
-    if not m_bytes or not m_inst or not m_hash or h.hexdigest()[:16] != m_hash.group(1):
+    if TRACE_NCU["sources"] != h.hexdigest()[:16]:
         return None, None
-    return int(m_bytes.group(1)), int(m_inst.group(1))
+    return TRACE_NCU["dram_bytes"], TRACE_NCU["warp_instructions"]
 
 
 class ClockSampler:
@@ -465,22 +463,28 @@ def run_ours(args):
     pipe.close()
 
     hbm, peak_kind = peaks()
+    # the dominant kernel (the trace, ~80% of a sorted step) against its
+    # algorithmic HBM floor: 48 B per ray (ray in, hit out) over the live
+    # CUDA-event duration of the launch
     trace_ach = BYTES_TRACE * n / (phase_ms["trace"] * 1e-3) / 1e9
-    traffic, inst = (None, None) if args.small else measured_trace_counts()
+    traffic, inst = (None, None) if args.small else trace_ncu_counts()
     sm_mhz = clocks.get("sm_mhz") or MAX_SM_MHZ
-    issue_peak = SMS * ISSUE_PER_SM_CYCLE * sm_mhz * 1e6 / 1e9  # G warp-instructions/s
+    roofline = {"bound": "hbm", "kernel": "trace (fused trace + length-table update)",
+                "achieved": round(trace_ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(trace_ach / hbm, 4),
+                "traffic": traffic, "peak_kind": peak_kind + " (MEASURED_PEAKS hbm_gbs, copy bandwidth)",
+                "algorithmic_bytes_per_ray": BYTES_TRACE, "units_per_launch": n,
+                "launch_ms": round(phase_ms["trace"], 4)}
+    if traffic is not None:
+        roofline["traffic_over_algorithmic"] = round(traffic / (BYTES_TRACE * n), 2)
     if inst is not None:
-        # the trace kernel is bound by instruction issue (see its ncu summary)
+        # what actually bounds the kernel: instruction issue (ncu warp instructions
+        # per launch over the live launch time, against 4 issue slots x 152 SMs
+        # x the sampled SM clock)
+        issue_peak = SMS * ISSUE_PER_SM_CYCLE * sm_mhz * 1e6 / 1e9
         ach = inst / (phase_ms["trace"] * 1e-3) / 1e9
-        roofline = {"bound": "alu", "kernel": "trace (fused trace + length-table update)",
-                    "achieved": round(ach, 1), "peak": round(issue_peak, 1),
-                    "unit": "G warp-instructions/s", "frac": round(ach / issue_peak, 4), "traffic": traffic,
-                    "work_per_launch": inst, "work_unit": "warp instructions (ncu smsp__inst_executed.sum)",
-                    "peak_kind": "derived: 4 issue slots x 152 SMs x sampled SM clock %.0f MHz" % sm_mhz}
-    else:
-        roofline = {"bound": "hbm", "kernel": "trace", "achieved": round(trace_ach, 1), "peak": hbm,
-                    "unit": "GB/s", "frac": round(trace_ach / hbm, 4), "traffic": None,
-                    "peak_kind": peak_kind, "algorithmic_bytes_per_ray": BYTES_TRACE}
+        roofline["issue"] = {"achieved": round(ach, 1), "peak": round(issue_peak, 1),
+                             "unit": "G warp-instructions/s", "frac": round(ach / issue_peak, 4),
+                             "warp_instructions_per_launch": inst}
     sort_ach = BYTES_SORT * n / (phase_ms["sort"] * 1e-3) / 1e9
     gather_ach = BYTES_GATHER * n / (phase_ms["gather"] * 1e-3) / 1e9
     key_ach = BYTES_KEY * n / (phase_ms["key"] * 1e-3) / 1e9
@@ -500,9 +504,6 @@ def run_ours(args):
         "speedup_vs_unsorted": round(value / unsorted, 3),
         "phases_ms": {k: round(v, 4) for k, v in phase_ms.items()},
         "roofline": roofline,
-        "trace_hbm": {"achieved": round(trace_ach, 1), "peak": hbm, "unit": "GB/s",
-                      "frac": round(trace_ach / hbm, 4), "algorithmic_bytes_per_ray": BYTES_TRACE,
-                      "peak_kind": peak_kind},
         "phase_roofline": {
             "key": {"gbs": round(key_ach, 1), "frac": round(key_ach / hbm, 3), "bytes_per_ray": BYTES_KEY},
             "sort": {"gbs": round(sort_ach, 1), "frac": round(sort_ach / hbm, 3), "bytes_per_ray": BYTES_SORT,
@@ -530,7 +531,7 @@ def run_ours(args):
         out["p99_at_load"] = "%.0f%% of measured capacity (%.1f requests/s)" % (100 * mid["load_frac"],
                                                                                 mid["offered_rps"])
     if rank == 0:
-        out["cpu_baseline"] = cpu_baseline(tris, lo, hi, sample=20000 if args.small else 100000)
+        out["cpu_baseline"] = cpu_baseline(tris, lo, hi, sample=20000 if args.small else 400000)
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -982,34 +983,105 @@ def bench_serving(args, dev, slots: int = 4, max_batch_rays: int = 1 << 23, frac
 
 # ----------------------------------------------------------------------------- oracle
 
-def oracle_bounce_time(tris, lo, hi, rays, obvh, table):
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def stable_merge(a, b):
+    """Stable merge of two sorted runs (keys, indices) where every index of `a`
+    precedes every index of `b`: an element's output position is its position
+    in its own run plus the number of elements of the other run that go before
+    it (equal keys of `a` go first)."""
+    ka, pa = a
+    kb, pb = b
+    pos_a = np.arange(ka.shape[0]) + np.searchsorted(kb, ka, side="left")
+    pos_b = np.arange(kb.shape[0]) + np.searchsorted(ka, kb, side="right")
+    k = np.empty(ka.shape[0] + kb.shape[0], ka.dtype)
+    p = np.empty(k.shape[0], pa.dtype)
+    k[pos_a], k[pos_b] = ka, kb
+    p[pos_a], p[pos_b] = pa, pb
+    return k, p
+
+
+def oracle_bounce(lo, hi, rays, obvh, table, threads: int = 1):
+    """One bounce through the oracle, as it stands: keys, stable sort, gather,
+    trace (the oracle's BVH) and the length-table update.  With threads > 1 the
+    same oracle functions run on contiguous ray ranges in parallel (ctypes
+    releases the GIL around every C call): keys, gather and trace by range;
+    the sort as a stable sort per range followed by stable pairwise merges of
+    neighbouring ranges (equal keys keep the lower indices first: the stable
+    order).  The table is
+    updated once, after the trace, as in the single-threaded run.  Returns
+    (keys, perm, hits)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     import oracle
-    t0 = time.perf_counter()
-    keys = oracle.compute_keys(oracle.TWO_POINT, KEY_BITS, rays.o_tmin, rays.d_tmax, lo, hi,
-                               tsrc=oracle.T_ADAPTIVE, table=table)
-    perm, _ = oracle.stable_sort(keys)
-    so, sd, sp = oracle.permute(rays.o_tmin, rays.d_tmax, rays.payload, perm)
-    h, _ = obvh.trace(so, sd)
+    n = rays.o_tmin.shape[0]
+    if threads <= 1:
+        keys = oracle.compute_keys(oracle.TWO_POINT, KEY_BITS, rays.o_tmin, rays.d_tmax, lo, hi,
+                                   tsrc=oracle.T_ADAPTIVE, table=table)
+        perm, _ = oracle.stable_sort(keys)
+        so, sd, sp = oracle.permute(rays.o_tmin, rays.d_tmax, rays.payload, perm)
+        h, _ = obvh.trace(so, sd)
+        table.accumulate(lo, hi, so, sd, h)
+        return keys, perm, h
+    cuts = [n * k // threads for k in range(threads + 1)]
+    ranges = [(cuts[k], cuts[k + 1]) for k in range(threads) if cuts[k + 1] > cuts[k]]
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(lambda r: oracle.compute_keys(oracle.TWO_POINT, KEY_BITS, rays.o_tmin[r[0]:r[1]],
+                                                          rays.d_tmax[r[0]:r[1]], lo, hi,
+                                                          tsrc=oracle.T_ADAPTIVE, table=table), ranges))
+        keys = np.concatenate(parts)
+        sorted_parts = list(ex.map(lambda r: oracle.stable_sort(keys[r[0]:r[1]]), ranges))
+        runs = [(sk, p + np.uint32(r[0])) for (p, sk), r in zip(sorted_parts, ranges)]
+        while len(runs) > 1:  # pairwise merges of neighbouring ranges, in parallel
+            pairs = [(runs[k], runs[k + 1]) for k in range(0, len(runs) - 1, 2)]
+            merged = list(ex.map(lambda ab: stable_merge(*ab), pairs))
+            runs = merged + ([runs[-1]] if len(runs) % 2 else [])
+        perm = runs[0][1]
+        gathered = list(ex.map(lambda r: oracle.permute(rays.o_tmin, rays.d_tmax, rays.payload,
+                                                        perm[r[0]:r[1]]), ranges))
+        so = np.concatenate([g[0] for g in gathered])
+        sd = np.concatenate([g[1] for g in gathered])
+        hits = list(ex.map(lambda r: obvh.trace(so[r[0]:r[1]], sd[r[0]:r[1]])[0], ranges))
+    h = np.concatenate(hits)
     table.accumulate(lo, hi, so, sd, h)
+    return keys, perm, h
+
+
+def oracle_bounce_time(lo, hi, rays, obvh, table, threads: int = 1):
+    t0 = time.perf_counter()
+    oracle_bounce(lo, hi, rays, obvh, table, threads)
     return time.perf_counter() - t0
 
 
 def cpu_baseline(tris, lo, hi, sample: int):
-    """The oracle (single thread) on a bounded sample of the same scene: a
-    trace-free stand-in secondary wavefront of `sample` rays."""
+    """The oracle on a bounded sample of the same scene (a trace-free stand-in
+    secondary wavefront of `sample` rays), on every host core and on one."""
     import oracle
     from paper_2506_11273_gb300 import workloads as W
     rays = W.surface_rays(tris, sample, seed=77)
     obvh = oracle.BVH(tris)
-    table = oracle.LengthTable(oracle.largest_extent(lo, hi))
-    dt = oracle_bounce_time(tris, lo, hi, rays, obvh, table)
-    return {"value": round(sample / dt / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+    cores = host_cores()
+    E = oracle.largest_extent(lo, hi)
+    dt = oracle_bounce_time(lo, hi, rays, obvh, oracle.LengthTable(E), threads=cores)
+    one = W.Rays(rays.o_tmin[: sample // 4], rays.d_tmax[: sample // 4], rays.payload[: sample // 4])
+    dt1 = oracle_bounce_time(lo, hi, one, obvh, oracle.LengthTable(E), threads=1)
+    return {"value": round(sample / dt / 1e6, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d stand-in secondary rays (origins on the scene by area, BSDF directions) of the "
-                      "same scene; keys+sort+gather+trace (oracle BVH)+accumulate, one thread" % sample,
-            "seconds": round(dt, 2)}
+                      "same scene; keys + sort + gather + trace (oracle BVH) + accumulate on %d threads "
+                      "(ray ranges; per-range stable sorts and stable pairwise merges)" % (sample, cores),
+            "seconds": round(dt, 2),
+            "single_thread": {"value": round(one.o_tmin.shape[0] / dt1 / 1e6, 4), "unit": UNIT, "cores": 1,
+                              "rays": int(one.o_tmin.shape[0]), "seconds": round(dt1, 2)}}
 
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands on the host's cores, on a
+    bounded sample of the same workload per step."""
     rank, world, local = dist_env()
     if rank != 0:
         return
@@ -1019,21 +1091,23 @@ def run_reference(args):
     lo, hi = W.scene_aabb(tris)
     obvh = oracle.BVH(tris)
     table = oracle.LengthTable(oracle.largest_extent(lo, hi))
-    sample = 5000 if args.small else 20000
+    cores = host_cores()
+    sample = 20000 if args.small else 200000
     rays = W.surface_rays(tris, sample, seed=77)
     for _ in range(args.warmup):
-        oracle_bounce_time(tris, lo, hi, rays, obvh, table)
-    ts = [oracle_bounce_time(tris, lo, hi, rays, obvh, table) for _ in range(args.steps)]
+        oracle_bounce_time(lo, hi, rays, obvh, table, threads=cores)
+    ts = [oracle_bounce_time(lo, hi, rays, obvh, table, threads=cores) for _ in range(args.steps)]
     value = sample * args.steps / sum(ts) / 1e6
-    desc = ("%d stand-in secondary rays per step (same scene), oracle keys+sort+gather+trace+accumulate, "
-            "one thread" % sample)
+    desc = ("%d stand-in secondary rays per step (same scene), oracle keys + sort + gather + trace + accumulate "
+            "on %d threads (ray ranges; per-range stable sorts and stable pairwise merges)" % (sample, cores))
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(ts) / args.steps, 2),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64",
            "data": "synthetic",
            "config": {"workload": "path tracer 1920x1080 1spp scene, %d-ray sample per step" % sample,
                       "key": "two_point_adaptive", "key_bits": KEY_BITS},
-           "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+           "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": desc},
            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

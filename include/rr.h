@@ -35,8 +35,10 @@
  *    no-op that returns RR_OK.
  *  - Failures inside kernels (a radix-sort look-back or a bulk copy that waited
  *    too long, a traversal stack overflow, an index out of range) never trap:
- *    the kernel records a flag in a per-device error word and finishes.
- *    rr_device_error() reads and clears it.
+ *    the kernel records a flag in the error word of the stream it runs on and
+ *    finishes.  rr_stream_error() reads and clears one stream's word without
+ *    synchronising; rr_device_error() synchronises the device and reads and
+ *    clears every word.
  *  - Ray layout (structure of arrays, 16-byte aligned):
  *      o_tmin  float4 per ray: origin.x, origin.y, origin.z, tmin
  *      d_tmax  float4 per ray: direction.x, .y, .z, tmax
@@ -66,7 +68,8 @@ typedef enum {
     RR_ERR_TIMEOUT = 4,     /* device: a bounded wait gave up (radix-sort look-back) */
     RR_ERR_STACK = 5,       /* device: a traversal stack would have overflowed */
     RR_ERR_UNSUPPORTED = 6, /* a valid request this build does not handle */
-    RR_ERR_TOO_LARGE = 7    /* n exceeds the fixed maximum of rr_sort_noalloc */
+    RR_ERR_TOO_LARGE = 7,   /* n exceeds the fixed maximum of rr_sort_noalloc */
+    RR_ERR_DEVICE = 8       /* a kernel of the work recorded a device error flag (served requests) */
 } rr_status;
 
 /* Device error flags accumulated in the per-device error word. */
@@ -220,8 +223,9 @@ rr_status rr_sort_segments(const void *keys_in, void *keys_out, uint32_t *perm_o
  * call's contents; each call clears what must start at zero before it uses it.
  * Calls whose work can overlap on the GPU (on different streams, or from host
  * threads without ordering between them) race on the array: serialise them.
- * The per-call error word lives in the array and is cleared by each call, so a
- * look-back timeout is not visible through rr_device_error().
+ * The error word of these calls lives in the array; a look-back wait that runs
+ * out sets RR_DEVERR_LOOKBACK_TIMEOUT there, where it stays until
+ * rr_device_error() reads and clears it (rr_stream_error() does not see it).
  */
 #define RR_SORT_NOALLOC_MAX_N (1u << 20)
 #define RR_SORT_NOALLOC_SCRATCH_BYTES (26u << 20)
@@ -250,6 +254,8 @@ rr_status rr_permute(const float *o_tmin_in, const float *d_tmax_in, const uint3
 rr_status rr_build_bvh(const float *tris_host, uint32_t n_tris, rr_bvh **out);
 rr_status rr_bvh_destroy(rr_bvh *bvh);
 rr_status rr_bvh_get_info(const rr_bvh *bvh, rr_bvh_info *info);
+/* The scene box: min and max over all vertices (the box the keys quantise in, Section 3). */
+rr_status rr_bvh_aabb(const rr_bvh *bvh, float lo[3], float hi[3]);
 
 /*
  * rr_trace - closest hit of every ray: the smallest t with tmin < t < tmax over
@@ -522,6 +528,9 @@ typedef struct {
     uint64_t start_ns;         /* admission (group enqueued), */
     uint64_t done_ns;          /* copy-out finished (host function ran) */
     uint32_t batch_requests;   /* requests in the group that carried this one */
+    uint32_t device_flags;     /* RR_DEVERR_* flags the group's kernels recorded (0: none); when
+                                  non-zero rr_server_wait returns RR_ERR_DEVICE for each request of
+                                  that group, and requests of other groups are unaffected */
 } rr_request_times;
 
 typedef struct {
@@ -584,7 +593,23 @@ rr_status rr_server_destroy(rr_server *srv);
  */
 rr_status rr_selftest_lookback_timeout(void *stream);
 
-/* Reads and clears the current device's error word (RR_DEVERR_* flags); synchronising. */
+/*
+ * rr_stream_error - reads and clears the error word of `stream`: the RR_DEVERR_*
+ * flags recorded by the library's kernels that ran on that stream (graphs of
+ * rr_batch_run report to the stream they are launched on).  Asynchronous: one
+ * kernel is enqueued on `stream` that writes the flags to *flags_out and
+ * clears the word, so the flags cover every library call enqueued on the
+ * stream before this one; read *flags_out after the stream has reached that
+ * point (e.g. cudaStreamSynchronize).  flags_out: 4 bytes of device memory or
+ * of page-locked host memory (cudaHostAlloc / cudaHostRegister); pageable
+ * memory returns RR_ERR_INVALID_ARG.  Each device keeps 1023 stream words;
+ * further streams share one extra word (their flags are then reported for
+ * all of them together).
+ */
+rr_status rr_stream_error(void *stream, uint32_t *flags_out);
+
+/* Synchronises the device, then reads and clears every stream's error word and
+ * the error word of rr_sort_noalloc, returning the union of their flags. */
 rr_status rr_device_error(uint32_t *flags_out);
 const char *rr_status_string(rr_status s);
 /* Message of the last failing call on this thread ("" if none). */

@@ -54,25 +54,70 @@ DeviceState *device_state(rr_status *st) {
         }
         d.sm_count = prop.multiProcessorCount;
         d.max_smem_optin = (int)prop.sharedMemPerBlockOptin;
-        // the error word and the trace queue counters live in one allocation
+        // the error words and the trace queue counters live in one allocation
+        const size_t words = kErrorWords + 2 * (size_t)(kQueueSlots + kCaptureQueueSlots);
         uint32_t *mem = nullptr;
-        e = cudaMalloc(&mem, sizeof(uint32_t) * (64 + kCounterPool));
+        e = cudaMalloc(&mem, sizeof(uint32_t) * words);
         if (e != cudaSuccess) {
             *st = fail_cuda(e, "device state allocation");
             return nullptr;
         }
-        e = cudaMemset(mem, 0, sizeof(uint32_t) * (64 + kCounterPool));
+        e = cudaMemset(mem, 0, sizeof(uint32_t) * words);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) {
             cudaFree(mem);
             *st = fail_cuda(e, "device state memset");
             return nullptr;
         }
         d.err = mem;
-        d.counters = mem + 64;
+        d.counters = mem + kErrorWords;
         g_dev_ready[dev] = true;
     }
     *st = RR_OK;
     return &d;
+}
+
+uint32_t *error_word(DeviceState *d, cudaStream_t s) {
+    unsigned long long id = 0;
+    if (cudaStreamGetId(s, &id) != cudaSuccess) {
+        cudaGetLastError();
+        return d->err;
+    }
+    std::lock_guard<std::mutex> lock(d->mu);
+    auto it = d->stream_words.find(id);
+    if (it != d->stream_words.end()) return d->err + it->second;
+    if (d->next_word >= kErrorWords) return d->err;  // every word taken: the shared word
+    const uint32_t w = d->next_word++;
+    d->stream_words.emplace(id, w);
+    return d->err + w;
+}
+
+rr_status with_trace_queue(DeviceState *d, cudaStream_t s, const std::function<rr_status(uint32_t *)> &launch) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return fail_cuda(e, "trace queue: capture status");
+    std::lock_guard<std::mutex> lock(d->mu);
+    if (cs != cudaStreamCaptureStatusNone) {
+        const uint64_t k = d->next_capture_queue++ % kCaptureQueueSlots;
+        return launch(d->counters + 2 * (kQueueSlots + k));
+    }
+    const uint64_t k = d->next_queue++ % kQueueSlots;
+    cudaEvent_t &ev = d->queue_done[k];
+    if (!ev) {
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            ev = nullptr;
+            return fail_cuda(e, "trace queue: event");
+        }
+    } else {
+        // the pair's previous launch (on any stream) must be finished first
+        e = cudaStreamWaitEvent(s, ev, 0);
+        if (e != cudaSuccess) return fail_cuda(e, "trace queue: wait");
+    }
+    const rr_status st = launch(d->counters + 2 * k);
+    if (st != RR_OK) return st;
+    e = cudaEventRecord(ev, s);
+    return e == cudaSuccess ? RR_OK : fail_cuda(e, "trace queue: record");
 }
 
 }  // namespace rr
@@ -84,13 +129,53 @@ extern "C" rr_status rr_device_error(uint32_t *flags_out) {
     rr_status st;
     DeviceState *d = device_state(&st);
     if (!d) return st;
-    uint32_t v = 0;
-    cudaError_t e = cudaMemcpy(&v, d->err, sizeof(v), cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail_cuda(e, "rr_device_error: synchronise");
+    uint32_t words[kErrorWords];
+    e = cudaMemcpy(words, d->err, sizeof(words), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return fail_cuda(e, "rr_device_error: read");
-    e = cudaMemset(d->err, 0, sizeof(uint32_t));
+    e = cudaMemset(d->err, 0, sizeof(words));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return fail_cuda(e, "rr_device_error: clear");
+    uint32_t v = take_noalloc_error();
+    for (uint32_t w : words) v |= w;
     *flags_out = v;
     return RR_OK;
+}
+
+namespace rr {
+namespace {
+__global__ void take_error_kernel(uint32_t *word, uint32_t *out) { *out = atomicExch(word, 0u); }
+}  // namespace
+
+rr_status enqueue_take_error(uint32_t *word, uint32_t *out, cudaStream_t s) {
+    take_error_kernel<<<1, 1, 0, s>>>(word, out);
+    note_launches(1);
+    return check_launch("device error word");
+}
+}  // namespace rr
+
+extern "C" rr_status rr_stream_error(void *stream, uint32_t *flags_out) {
+    if (!flags_out || !aligned(flags_out, 4)) return fail(RR_ERR_INVALID_ARG, "rr_stream_error: NULL or misaligned output");
+    rr_status st;
+    DeviceState *d = device_state(&st);
+    if (!d) return st;
+    // the flags are written by a kernel: device memory or page-locked host memory
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, flags_out) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RR_ERR_INVALID_ARG, "rr_stream_error: output is not device-accessible memory");
+    }
+    uint32_t *out = nullptr;
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+        out = flags_out;
+    else if (a.type == cudaMemoryTypeHost)
+        out = static_cast<uint32_t *>(a.devicePointer);
+    if (!out)
+        return fail(RR_ERR_INVALID_ARG,
+                    "rr_stream_error: output must be device memory or page-locked host memory");
+    cudaStream_t s = as_stream(stream);
+    return enqueue_take_error(error_word(d, s), out, s);
 }
 
 extern "C" const char *rr_status_string(rr_status s) {
@@ -103,6 +188,7 @@ extern "C" const char *rr_status_string(rr_status s) {
         case RR_ERR_STACK: return "traversal stack overflow";
         case RR_ERR_UNSUPPORTED: return "unsupported";
         case RR_ERR_TOO_LARGE: return "size exceeds the fixed maximum of the no-allocation entry point";
+        case RR_ERR_DEVICE: return "a kernel recorded a device error flag";
     }
     return "unknown status";
 }

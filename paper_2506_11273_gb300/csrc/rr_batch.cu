@@ -26,6 +26,7 @@ struct GraphEntry {
     const float *o, *d;
     float *hits;
     uint32_t *perm;
+    uint32_t *err;  // error word of the stream the graph reports to
     cudaGraphExec_t exec;
 };
 
@@ -83,21 +84,23 @@ rr_t_source run_tsrc(const rr_batch *b, const rr_batch_config &c) {
     return l == RR_KEY_TWO_POINT && l == b->layout ? b->tsrc : RR_T_FIXED;
 }
 
-// The whole chain on one stream: keys, sort, trace.
+// The whole chain on one stream: keys, sort, trace.  Device errors go to
+// `err` (the word of the stream the chain is replayed on, not the capture
+// stream's).
 rr_status enqueue_batch(rr_batch *b, const float *o, const float *d, float *hits, uint32_t *perm,
-                        const rr_batch_config &c, cudaStream_t s) {
+                        const rr_batch_config &c, uint32_t *err, int sm_count, cudaStream_t s) {
     if (c.key_bits == 0)  // no reordering: every ray traced in input order
         return launch_trace_batch(b->d_segs, b->d_offsets, b->n_fronts, o, d, nullptr, b->n_total, hits,
-                                  accumulating(b), c.trace_block, b->queue, s);
+                                  accumulating(b), c.trace_block, b->queue, err, s);
     rr_status st = launch_keys_batch(b->d_segs, b->d_offsets, b->n_fronts, run_layout(b, c), run_tsrc(b, c), b->ratio,
                                      c.key_bits,
                                      b->seg_bits, o, d, b->n_total, b->keys, s);
     if (st != RR_OK) return st;
-    st = rr_sort(b->keys, nullptr, perm, b->n_total, c.key_bits + b->seg_bits, c.radix_bits, b->sort_ws,
-                 b->sort_ws_bytes, s);
+    st = sort_enqueue(b->keys, nullptr, perm, b->n_total, c.key_bits + b->seg_bits, c.radix_bits, b->sort_ws, err,
+                      sm_count, s);
     if (st != RR_OK) return st;
     return launch_trace_batch(b->d_segs, b->d_offsets, b->n_fronts, o, d, perm, b->n_total, hits, accumulating(b),
-                              c.trace_block, b->queue, s);
+                              c.trace_block, b->queue, err, s);
 }
 
 rr_status check_run_args(const rr_batch *b, const float *o, const float *d, const float *hits,
@@ -259,9 +262,14 @@ extern "C" rr_status rr_batch_run(rr_batch *b, const float *o_tmin, const float 
     if (st != RR_OK || b->n_total == 0) return st;
     uint32_t *perm = perm_out ? perm_out : b->perm;
     if (!aligned(perm, 4)) return fail(RR_ERR_INVALID_ARG, "rr_batch_run: perm misaligned");
+    DeviceState *ds = device_state(&st);
+    if (!ds) return st;
+    uint32_t *err = error_word(ds, as_stream(stream));
     GraphEntry *g = nullptr;
     for (GraphEntry &x : b->graphs)
-        if (same_cfg(x.cfg, *cfg) && x.o == o_tmin && x.d == d_tmax && x.hits == hits_out && x.perm == perm) g = &x;
+        if (same_cfg(x.cfg, *cfg) && x.o == o_tmin && x.d == d_tmax && x.hits == hits_out && x.perm == perm &&
+            x.err == err)
+            g = &x;
     if (!g) {
         if (b->graphs.size() >= kMaxGraphs) {  // keep the cache bounded: drop the oldest graph
             cudaGraphExecDestroy(b->graphs.front().exec);
@@ -270,7 +278,7 @@ extern "C" rr_status rr_batch_run(rr_batch *b, const float *o_tmin, const float 
         // capture the chain once for these buffers and this configuration
         cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return fail_cuda(e, "rr_batch_run: begin capture");
-        st = enqueue_batch(b, o_tmin, d_tmax, hits_out, perm, *cfg, b->capture);
+        st = enqueue_batch(b, o_tmin, d_tmax, hits_out, perm, *cfg, err, ds->sm_count, b->capture);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(b->capture, &graph);
         if (st != RR_OK) {
@@ -282,7 +290,7 @@ extern "C" rr_status rr_batch_run(rr_batch *b, const float *o_tmin, const float 
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return fail_cuda(e, "rr_batch_run: instantiate");
-        b->graphs.push_back(GraphEntry{*cfg, o_tmin, d_tmax, hits_out, perm, exec});
+        b->graphs.push_back(GraphEntry{*cfg, o_tmin, d_tmax, hits_out, perm, err, exec});
         g = &b->graphs.back();
     }
     const cudaError_t e = cudaGraphLaunch(g->exec, as_stream(stream));

@@ -33,9 +33,14 @@ rr_status launch_keys_batch(const BatchScene *segs, const uint32_t *seg_offsets,
 
 // Closest-hit trace of a batch through `order`, hits in input order; the
 // length tables of the segments are updated when `accumulate`.  queue: two
-// device words at zero, owned by the caller.
+// device words at zero, owned by the caller.  err: the error word the kernel
+// reports to.
 rr_status launch_trace_batch(const BatchScene *segs, const uint32_t *seg_offsets, uint32_t n_segs, const float *o_tmin,
                              const float *d_tmax, const uint32_t *order, uint32_t n, float *hits_out,
-                             bool accumulate, uint32_t block, uint32_t *queue, cudaStream_t s);
+                             bool accumulate, uint32_t block, uint32_t *queue, uint32_t *err, cudaStream_t s);
+
+// rr_sort with arguments already checked and device errors reported to `err`.
+rr_status sort_enqueue(const void *keys_in, void *keys_out, uint32_t *perm_out, uint32_t n, uint32_t bits,
+                       uint32_t radix_bits, void *workspace, uint32_t *err, int sm_count, cudaStream_t s);
 
 }  // namespace rr

@@ -5,7 +5,10 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <functional>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 
 #include "../../include/rr.h"
 
@@ -22,18 +25,51 @@ rr_status fail_cuda(cudaError_t e, const char *what);
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// Per-device state: the error word and cached properties.
+// Per-device state: error words, trace work-queue counters, cached properties.
+//
+// Error words: kernels OR RR_DEVERR_* flags into the word of the stream they
+// run on (word 0 is shared by the streams beyond the first kErrorWords - 1),
+// so rr_stream_error can tell one stream's failures from another's.
+//
+// Trace work queues: a persistent trace launch needs a pair of counter words
+// that no concurrent launch shares (the last block resets them).  Launches
+// take pairs round-robin from kQueueSlots; each pair's last launch records an
+// event, and the next launch that takes the pair waits for it on its own
+// stream, so two launches can never share a pair at the same time.  Launches
+// under stream capture take pairs from a separate ring of kCaptureQueueSlots
+// without events (a captured trace must not run concurrently with itself).
+constexpr uint32_t kErrorWords = 1024;
+constexpr uint32_t kQueueSlots = 2048;
+constexpr uint32_t kCaptureQueueSlots = 1024;
+
 struct DeviceState {
-    uint32_t *err = nullptr;      // device word with RR_DEVERR_* flags
-    uint32_t *counters = nullptr;  // pool of trace work-queue counters (zero at rest)
+    uint32_t *err = nullptr;       // kErrorWords device words of RR_DEVERR_* flags
+    uint32_t *counters = nullptr;  // 2 * (kQueueSlots + kCaptureQueueSlots) queue words (zero at rest)
     int sm_count = 0;
     int max_smem_optin = 0;
-    std::atomic<uint32_t> next_counter{0};
+    std::mutex mu;
+    std::unordered_map<unsigned long long, uint32_t> stream_words;  // stream id -> error word
+    uint32_t next_word = 1;
+    cudaEvent_t queue_done[kQueueSlots] = {};
+    uint64_t next_queue = 0, next_capture_queue = 0;
 };
-constexpr uint32_t kCounterPool = 4096;
 
 // Returns the state of the current device (initialised on first use) or null.
 DeviceState *device_state(rr_status *st);
+
+// The error word of stream `s` on this device (never null).
+uint32_t *error_word(DeviceState *d, cudaStream_t s);
+
+// Runs `launch(queue)` with a trace work-queue pair no concurrent launch
+// holds, and records the pair's completion event after it (see above).
+rr_status with_trace_queue(DeviceState *d, cudaStream_t s, const std::function<rr_status(uint32_t *)> &launch);
+
+// Reads and clears the error word of rr_sort_noalloc (defined with it).
+uint32_t take_noalloc_error();
+
+// Enqueues on `s`: *out = the flags of `word`, and `word` cleared.  out:
+// device-accessible (device or page-locked host memory).
+rr_status enqueue_take_error(uint32_t *word, uint32_t *out, cudaStream_t s);
 
 // Counts kernel launches made by the library.
 void note_launches(uint32_t k);

@@ -119,10 +119,12 @@ __global__ void __launch_bounds__(kKeyTile, 6) key_kernel(KeyArgs a) {
         if (tid == 0 && next < tiles) issue(next, buf ^ 1u);
         const bool ok = mbar_wait_bounded(&s_bar[buf], parity, kCopySpinLimit);
         if (!__syncthreads_and(ok)) {
-            // give up on this launch; let the copy already issued for the
-            // next tile land before the block's shared memory goes away
+            // give up on this launch; let the copies in flight (the late one
+            // into `buf` and the one already issued for the next tile) land
+            // before the block's shared memory goes away
             if (tid == 0) {
                 atomicOr(a.err, RR_DEVERR_COPY_TIMEOUT);
+                mbar_wait_bounded(&s_bar[buf], parity, kCopySpinLimit);
                 if (next < tiles) mbar_wait_bounded(&s_bar[buf ^ 1u], ((k + 1) >> 1) & 1u, kCopySpinLimit);
             }
             break;
@@ -344,9 +346,9 @@ extern "C" rr_status rr_compute_keys(const float *o_tmin, const float *d_tmax, u
     rr_status st;
     DeviceState *ds = device_state(&st);
     if (!ds) return st;
-    a.err = ds->err;
-    const int sms = ds->sm_count;
     cudaStream_t s = as_stream(stream);
+    a.err = error_word(ds, s);
+    const int sms = ds->sm_count;
     if (p->layout == RR_KEY_AILA) {
         launch_keys<RR_KEY_AILA, 0>(a, wide, sms, s);
     } else if (p->layout == RR_KEY_AILA_COMPACT) {

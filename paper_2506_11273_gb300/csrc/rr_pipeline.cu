@@ -233,8 +233,10 @@ extern "C" rr_status rr_pipeline_submit_host(rr_pipeline *p, const float *o_host
         e = cudaStreamWaitEvent(p->side, h.consumed, 0);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(payload_out_host, h.payload_sorted, 4ull * n, cudaMemcpyDeviceToHost, p->side);
-        if (e == cudaSuccess) e = cudaEventRecord(h.pay_down, p->side);
     }
+    // recorded for every submission, so that it also covers the payload
+    // downloads of earlier submissions still running on the side stream
+    if (e == cudaSuccess) e = cudaEventRecord(h.pay_down, p->side);
     if (e == cudaSuccess && !hits_direct) e = cudaMemcpyAsync(hits_host, h.hits, 16ull * n, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaEventRecord(h.done, s);
     if (e != cudaSuccess) return fail_cuda(e, "rr_pipeline_submit_host: download");
@@ -247,7 +249,9 @@ extern "C" rr_status rr_pipeline_wait(rr_pipeline *p, uint64_t ticket) {
     if (ticket == 0) return RR_OK;  // an empty submission
     if (ticket > p->submitted) return fail(RR_ERR_INVALID_ARG, "rr_pipeline_wait: ticket was never issued");
     // a slot's events are re-recorded by later submissions; those complete
-    // after this one, so waiting on them is never too early
+    // after this one, so waiting on them is never too early.  `done` follows
+    // every earlier submission on the caller's stream and `pay_down` every
+    // earlier payload download on the side stream.
     HostSlot &h = p->slot[(ticket - 1) & 1];
     cudaError_t e = cudaEventSynchronize(h.done);
     if (e == cudaSuccess) e = cudaEventSynchronize(h.pay_down);

@@ -52,6 +52,8 @@ struct Group;
 struct Slot {
     cudaStream_t stream = nullptr;
     uint32_t *queue = nullptr;       // trace work-queue words of this slot
+    uint32_t *err = nullptr;         // device error word of the slot's stream
+    uint32_t *h_err = nullptr;       // pinned: the flags of the slot's last group, read after its copy-out
     BatchScene *h_segs = nullptr;    // pinned staging of the group's descriptors
     uint32_t *h_offs = nullptr;      // and offsets (one group in flight per slot)
     Group *busy = nullptr;
@@ -83,6 +85,7 @@ struct rr_server {
     std::thread worker;
     uint64_t batches = 0, max_group = 0, peak_reserved = 0;
     std::string worker_error;
+    int sm_count = 0;
 };
 
 namespace {
@@ -110,8 +113,15 @@ void CUDART_CB group_done(void *p) {
     Group *g = static_cast<Group *>(p);
     rr_server *s = g->server;
     const uint64_t t = now_ns();
+    // the flags the group's kernels recorded on the slot's stream (taken from
+    // its error word after the copy-out): they fail this group's requests only
+    const uint32_t flags = *static_cast<volatile uint32_t *>(s->slots[g->slot].h_err);
     std::lock_guard<std::mutex> lock(s->mu);
-    for (Request *r : g->reqs) r->times.done_ns = t;
+    for (Request *r : g->reqs) {
+        r->times.done_ns = t;
+        r->times.device_flags = flags;
+        if (flags) r->status = RR_ERR_DEVICE;
+    }
     s->finished.push_back(g);
     s->cv.notify_all();
 }
@@ -166,10 +176,11 @@ rr_status launch_group(rr_server *s, Group *g) {
         rs = launch_keys_batch(segs, offs, ng, (rr_key_layout)s->cfg.layout, (rr_t_source)s->cfg.t_source,
                                s->cfg.ratio, key_bits, seg_bits, o, d, (uint32_t)n, keys, st);
         if (rs == RR_OK)
-            rs = rr_sort(keys, nullptr, perm, (uint32_t)n, total_bits, s->cfg.radix_bits, wsp, ws, st);
+            rs = sort_enqueue(keys, nullptr, perm, (uint32_t)n, total_bits, s->cfg.radix_bits, wsp, sl.err,
+                              s->sm_count, st);
         if (rs == RR_OK)
             rs = launch_trace_batch(segs, offs, ng, o, d, perm, (uint32_t)n, hits, adaptive(s),
-                                    s->cfg.trace_block, sl.queue, st);
+                                    s->cfg.trace_block, sl.queue, sl.err, st);
     }
     at = 0;
     for (uint32_t k = 0; k < ng && rs == RR_OK && e == cudaSuccess; ++k) {
@@ -180,6 +191,8 @@ rr_status launch_group(rr_server *s, Group *g) {
     cudaFreeAsync(mem, st);
     if (rs != RR_OK) return rs;
     if (e != cudaSuccess) return fail_cuda(e, "rr_server: copy-out");
+    rs = enqueue_take_error(sl.err, sl.h_err, st);
+    if (rs != RR_OK) return rs;
     e = cudaLaunchHostFunc(st, group_done, g);
     if (e != cudaSuccess) return fail_cuda(e, "rr_server: host function");
     return RR_OK;
@@ -287,14 +300,19 @@ extern "C" rr_status rr_server_create(const rr_server_config *cfg, rr_server **o
     if (cfg->max_batch_rays < 1 || cfg->max_batch_rays >= (1u << 30))
         return fail(RR_ERR_INVALID_ARG, "rr_server_create: max_batch_rays must be 1..2^30-1");
     rr_status st;
-    if (!device_state(&st)) return st;
+    DeviceState *ds = device_state(&st);
+    if (!ds) return st;
     rr_server *s = new rr_server();
     cudaGetDevice(&s->device);
     s->cfg = *cfg;
+    s->sm_count = ds->sm_count;
     s->slots.resize(cfg->slots);
     cudaError_t e = cudaSuccess;
     for (Slot &sl : s->slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) sl.err = error_word(ds, sl.stream);
+        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&sl.h_err), sizeof(uint32_t));
+        if (e == cudaSuccess) *sl.h_err = 0u;
         if (e == cudaSuccess) e = cudaMalloc(&sl.queue, 2 * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMemset(sl.queue, 0, 2 * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&sl.h_segs), sizeof(BatchScene) * kMaxBatchSegments);
@@ -321,6 +339,7 @@ extern "C" rr_status rr_server_create(const rr_server_config *cfg, rr_server **o
             cudaFree(sl.queue);
             cudaFreeHost(sl.h_segs);
             cudaFreeHost(sl.h_offs);
+            cudaFreeHost(sl.h_err);
         }
         delete s;
         return fail_cuda(e, "rr_server_create");
@@ -416,6 +435,7 @@ extern "C" rr_status rr_server_wait(rr_server *s, uint64_t ticket, double timeou
     const rr_status st = r->status;
     s->all.erase(it);
     delete r;
+    if (st == RR_ERR_DEVICE) return fail(st, "rr_server_wait: a kernel of the request's group set a device error flag");
     if (st != RR_OK) return fail(st, "rr_server_wait: request failed: " + s->worker_error);
     return RR_OK;
 }
@@ -445,6 +465,7 @@ extern "C" rr_status rr_server_destroy(rr_server *s) {
         cudaFree(sl.queue);
         cudaFreeHost(sl.h_segs);
         cudaFreeHost(sl.h_offs);
+        cudaFreeHost(sl.h_err);
     }
     for (auto &kv : s->all) delete kv.second;
     delete s;

@@ -606,6 +606,25 @@ static rr_status run_sort(const SortPlan &pl, const K *keys_in, K *keys_out, uin
     return RR_OK;
 }
 
+// The sort of rr_sort (arguments already checked) with device errors going to
+// `err`: batches captured on one stream and replayed on another report to the
+// word of the stream they run on.
+rr_status sort_enqueue(const void *keys_in, void *keys_out, uint32_t *perm_out, uint32_t n, uint32_t bits,
+                       uint32_t radix_bits, void *workspace, uint32_t *err, int sm_count, cudaStream_t s) {
+    const SortPlan pl = plan_sort(n, bits, radix_bits);
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    if (pl.kb == 4) {
+        const uint32_t *ki = static_cast<const uint32_t *>(keys_in);
+        uint32_t *ko = static_cast<uint32_t *>(keys_out);
+        return radix_bits == 8 ? run_sort<uint32_t, 8>(pl, ki, ko, perm_out, n, bits, ws, err, sm_count, s)
+                               : run_sort<uint32_t, 4>(pl, ki, ko, perm_out, n, bits, ws, err, sm_count, s);
+    }
+    const unsigned long long *ki = static_cast<const unsigned long long *>(keys_in);
+    unsigned long long *ko = static_cast<unsigned long long *>(keys_out);
+    return radix_bits == 8 ? run_sort<unsigned long long, 8>(pl, ki, ko, perm_out, n, bits, ws, err, sm_count, s)
+                           : run_sort<unsigned long long, 4>(pl, ki, ko, perm_out, n, bits, ws, err, sm_count, s);
+}
+
 }  // namespace rr
 
 using namespace rr;
@@ -642,18 +661,8 @@ extern "C" rr_status rr_sort(const void *keys_in, void *keys_out, uint32_t *perm
     DeviceState *ds = device_state(&st);
     if (!ds) return st;
     cudaStream_t s = as_stream(stream);
-    unsigned char *ws = static_cast<unsigned char *>(workspace);
-    if (pl.kb == 4) {
-        const uint32_t *ki = static_cast<const uint32_t *>(keys_in);
-        uint32_t *ko = static_cast<uint32_t *>(keys_out);
-        return radix_bits == 8 ? run_sort<uint32_t, 8>(pl, ki, ko, perm_out, n, bits, ws, ds->err, ds->sm_count, s)
-                               : run_sort<uint32_t, 4>(pl, ki, ko, perm_out, n, bits, ws, ds->err, ds->sm_count, s);
-    }
-    const unsigned long long *ki = static_cast<const unsigned long long *>(keys_in);
-    unsigned long long *ko = static_cast<unsigned long long *>(keys_out);
-    return radix_bits == 8
-               ? run_sort<unsigned long long, 8>(pl, ki, ko, perm_out, n, bits, ws, ds->err, ds->sm_count, s)
-               : run_sort<unsigned long long, 4>(pl, ki, ko, perm_out, n, bits, ws, ds->err, ds->sm_count, s);
+    return sort_enqueue(keys_in, keys_out, perm_out, n, bits, radix_bits, workspace, error_word(ds, s),
+                        ds->sm_count, s);
 }
 
 extern "C" rr_status rr_sort_segments(const void *keys_in, void *keys_out, uint32_t *perm_out, uint32_t n,
@@ -724,7 +733,7 @@ extern "C" rr_status rr_selftest_lookback_timeout(void *stream) {
         a.hist = reinterpret_cast<const uint32_t *>(ws + pl.off_hist);
         a.lookback = reinterpret_cast<unsigned long long *>(ws + pl.off_lookback);
         a.tile_counter = counter;
-        a.err = ds->err;
+        a.err = error_word(ds, s);
         onesweep_kernel<K, 8, 3><<<1, kSortBlock, pass_smem<K, 8>(), s>>>(a);
         note_launches(1);
         e = cudaGetLastError();
@@ -799,11 +808,26 @@ static rr_status launch_sort_noalloc(const SortPlan &pl, const K *keys_in, K *ke
                                      uint32_t n, uint32_t bits, unsigned char *scratch, int sm_count,
                                      cudaStream_t s) {
     // the array keeps the last call's contents: the counting kernel clears the
-    // error word, the tile counters and the look-back words before the passes
+    // tile counters and the look-back words before the passes.  The error word
+    // at the head of the array is not cleared: its flags stay until
+    // rr_device_error reads them (take_noalloc_error).
     uint32_t *err = reinterpret_cast<uint32_t *>(scratch);
     const cudaError_t e = enqueue_sort<K, RBITS>(pl, keys_in, keys_out, perm_out, n, bits, scratch + kNoAllocHeader,
-                                                 err, err, sm_count, s);
+                                                 err, nullptr, sm_count, s);
     return e == cudaSuccess ? RR_OK : RR_ERR_CUDA;
+}
+
+// Reads and clears the error word of rr_sort_noalloc on the current device
+// (synchronous copies of four bytes; used by rr_device_error).
+uint32_t take_noalloc_error() {
+    uint32_t v = 0;
+    const uint32_t zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_sort_scratch, sizeof(v), 0, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_sort_scratch, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
 }
 
 }  // namespace rr

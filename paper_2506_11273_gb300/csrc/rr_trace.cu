@@ -502,6 +502,15 @@ extern "C" rr_status rr_bvh_get_info(const rr_bvh *b, rr_bvh_info *info) {
     return RR_OK;
 }
 
+extern "C" rr_status rr_bvh_aabb(const rr_bvh *b, float lo[3], float hi[3]) {
+    if (!b || !lo || !hi) return fail(RR_ERR_INVALID_ARG, "rr_bvh_aabb: NULL argument");
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = b->info.aabb_lo[c];
+        hi[c] = b->info.aabb_hi[c];
+    }
+    return RR_OK;
+}
+
 namespace {
 
 template <bool ACC, bool ANY, bool MULTI, int BLOCK>
@@ -544,7 +553,7 @@ rr_status launch_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax
     rr_status st;
     DeviceState *ds = device_state(&st);
     if (!ds) return st;
-    const uint32_t slot = ds->next_counter.fetch_add(1) % (kCounterPool / 2);
+    cudaStream_t s = as_stream(stream);
     TraceArgs a{};
     a.scene.nodes = reinterpret_cast<const float4 *>(b->nodes);
     a.scene.tris = reinterpret_cast<const float4 *>(b->tris);
@@ -555,22 +564,23 @@ rr_status launch_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax
     a.hits = reinterpret_cast<float4 *>(hits_out);
     a.order = order;
     a.n = n;
-    a.queue = ds->counters + 2 * slot;
-    a.err = ds->err;
+    a.err = error_word(ds, s);
     a.table = table ? table->cells : nullptr;
     for (int c = 0; c < 3; ++c) {
         a.tlo[c] = table ? table->box.lo[c] : 0.0f;
         a.thi[c] = table ? table->box.hi[c] : 0.0f;
     }
-    cudaStream_t s = as_stream(stream);
-    if (table)
-        trace_enqueue<true, false, false, kTraceBlock>(a, ds->sm_count, s);
-    else if (any)
-        trace_enqueue<false, true, false, kTraceBlock>(a, ds->sm_count, s);
-    else
-        trace_enqueue<false, false, false, kTraceBlock>(a, ds->sm_count, s);
-    note_launches(1);
-    return check_launch(what);
+    return with_trace_queue(ds, s, [&](uint32_t *queue) {
+        a.queue = queue;
+        if (table)
+            trace_enqueue<true, false, false, kTraceBlock>(a, ds->sm_count, s);
+        else if (any)
+            trace_enqueue<false, true, false, kTraceBlock>(a, ds->sm_count, s);
+        else
+            trace_enqueue<false, false, false, kTraceBlock>(a, ds->sm_count, s);
+        note_launches(1);
+        return check_launch(what);
+    });
 }
 
 }  // namespace
@@ -579,7 +589,7 @@ namespace rr {
 
 rr_status launch_trace_batch(const BatchScene *segs, const uint32_t *seg_offsets, uint32_t n_segs, const float *o_tmin,
                              const float *d_tmax, const uint32_t *order, uint32_t n, float *hits_out,
-                             bool accumulate, uint32_t block, uint32_t *queue, cudaStream_t s) {
+                             bool accumulate, uint32_t block, uint32_t *queue, uint32_t *err, cudaStream_t s) {
     rr_status st;
     DeviceState *ds = device_state(&st);
     if (!ds) return st;
@@ -590,7 +600,7 @@ rr_status launch_trace_batch(const BatchScene *segs, const uint32_t *seg_offsets
     a.order = order;
     a.n = n;
     a.queue = queue;
-    a.err = ds->err;
+    a.err = err;
     a.segs = segs;
     a.seg_offsets = seg_offsets;
     a.n_segs = n_segs;

@@ -37,7 +37,8 @@ MISS = 0xFFFFFFFF
 TABLE_CELLS = 1 << 20
 
 STATUS = {0: "RR_OK", 1: "RR_ERR_INVALID_ARG", 2: "RR_ERR_CUDA", 3: "RR_ERR_OOM",
-          4: "RR_ERR_TIMEOUT", 5: "RR_ERR_STACK", 6: "RR_ERR_UNSUPPORTED", 7: "RR_ERR_TOO_LARGE"}
+          4: "RR_ERR_TIMEOUT", 5: "RR_ERR_STACK", 6: "RR_ERR_UNSUPPORTED", 7: "RR_ERR_TOO_LARGE",
+          8: "RR_ERR_DEVICE"}
 RR_SORT_NOALLOC_MAX_N = 1 << 20
 
 # every symbol include/rr.h declares
@@ -52,7 +53,7 @@ EXPORTS = [
     "rr_coherence_capsule", "rr_trace_ex", "rr_sort_segments", "rr_batch_create", "rr_batch_destroy",
     "rr_batch_info", "rr_batch_run", "rr_batch_run_loop", "rr_batch_tune", "rr_server_create",
     "rr_server_add_scene", "rr_server_submit", "rr_server_wait", "rr_server_stats", "rr_server_destroy",
-    "rr_selftest_lookback_timeout",
+    "rr_selftest_lookback_timeout", "rr_stream_error", "rr_bvh_aabb",
 ]
 
 
@@ -90,7 +91,7 @@ class ServerConfig(C.Structure):
 
 class RequestTimes(C.Structure):
     _fields_ = [("submit_ns", C.c_uint64), ("start_ns", C.c_uint64), ("done_ns", C.c_uint64),
-                ("batch_requests", C.c_uint32)]
+                ("batch_requests", C.c_uint32), ("device_flags", C.c_uint32)]
 
 
 class ServerStats(C.Structure):
@@ -155,6 +156,8 @@ def lib():
             L.rr_selftest_lookback_timeout.argtypes = [vp]
             L.rr_coherence_capsule.argtypes = [vp, vp, vp, u32, u32, C.c_float, vp, vp]
             L.rr_device_error.argtypes = [C.POINTER(C.c_uint32)]
+            L.rr_stream_error.argtypes = [vp, vp]
+            L.rr_bvh_aabb.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
             L.rr_status_string.argtypes = [i32]
             L.rr_status_string.restype = C.c_char_p
             L.rr_last_error_message.argtypes = []
@@ -549,7 +552,7 @@ class Server:
         _check(lib().rr_server_wait(self.handle, ticket, timeout_s, C.byref(tm)), "rr_server_wait")
         self._held.pop(ticket, None)
         return dict(submit_ns=tm.submit_ns, start_ns=tm.start_ns, done_ns=tm.done_ns,
-                    batch_requests=tm.batch_requests)
+                    batch_requests=tm.batch_requests, device_flags=tm.device_flags)
 
     def stats(self) -> dict:
         st = ServerStats()
@@ -595,6 +598,21 @@ def rr_device_error() -> int:
     v = C.c_uint32()
     _check(lib().rr_device_error(C.byref(v)), "rr_device_error")
     return int(v.value)
+
+
+def rr_stream_error(flags_out, stream=None):
+    """Enqueues on `stream` the read-and-clear of its error word into flags_out
+    (a CUDA int32 tensor of one element, or a pinned CPU one); read it after
+    the stream has synchronised."""
+    if flags_out.dtype != torch.int32 or flags_out.numel() < 1:
+        raise ValueError("flags_out must hold one int32")
+    _check(lib().rr_stream_error(_stream(stream), flags_out.data_ptr()), "rr_stream_error")
+
+
+def rr_bvh_aabb(bvh: "BVH"):
+    lo, hi = (C.c_float * 3)(), (C.c_float * 3)()
+    _check(lib().rr_bvh_aabb(bvh.handle, lo, hi), "rr_bvh_aabb")
+    return np.array(lo[:], np.float32), np.array(hi[:], np.float32)
 
 
 def rr_kernel_launch_count() -> int:

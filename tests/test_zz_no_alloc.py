@@ -56,6 +56,8 @@ def test_noalloc_sort_matches_rr_sort_on_two_calls_in_a_row():
         assert np.array_equal(p, p_ref)
         assert np.array_equal(k, k_ref)
         assert np.all(k[1:] >= k[:-1])
+    # the calls' error word (inside the array) is read by rr_device_error
+    assert rr.rr_device_error() == 0
 
 
 def test_noalloc_sort_rejects_sizes_beyond_its_maximum():
