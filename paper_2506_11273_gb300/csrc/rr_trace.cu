@@ -235,45 +235,43 @@ __device__ __forceinline__ bool ray_visit_node(RayState &r, uint2 *stack, const 
     return true;
 }
 
-// Tests every triangle of the pending group.  ANY: the first hit ends the ray
-// (the pending group, the current node group and the stack are dropped).
+// Tests the nearest-slot triangle of the pending group (one triangle per
+// traversal step).  ANY: a hit ends the ray (the pending group, the current
+// node group and the stack are dropped).
 template <bool ANY>
-__device__ __forceinline__ void ray_test_triangles(RayState &r, const SceneRef &a) {
+__device__ __forceinline__ void test_one_triangle(RayState &r, const SceneRef &a) {
     const float tmin = r.o.w;
-    while (r.t_hits != 0u) {
-        const uint32_t b = __ffs(r.t_hits) - 1u;
-        r.t_hits &= r.t_hits - 1u;
-        const uint32_t k = r.t_base + __popc(r.t_all & ((1u << b) - 1u));
-        const float4 *tp = a.tris + 3 * (size_t)k;
-        const float4 v0 = __ldg(tp), e1 = __ldg(tp + 1), e2 = __ldg(tp + 2);
-        const float4 d = r.d, o = r.o;
-        const float pvx = d.y * e2.z - d.z * e2.y;
-        const float pvy = d.z * e2.x - d.x * e2.z;
-        const float pvz = d.x * e2.y - d.y * e2.x;
-        const float det = e1.x * pvx + e1.y * pvy + e1.z * pvz;
-        if (det == 0.0f) continue;
-        const float inv = __frcp_rn(det);
-        const float tvx = o.x - v0.x, tvy = o.y - v0.y, tvz = o.z - v0.z;
-        const float u = (tvx * pvx + tvy * pvy + tvz * pvz) * inv;
-        if (!(u >= 0.0f && u <= 1.0f)) continue;
-        const float qvx = tvy * e1.z - tvz * e1.y;
-        const float qvy = tvz * e1.x - tvx * e1.z;
-        const float qvz = tvx * e1.y - tvy * e1.x;
-        const float v = (d.x * qvx + d.y * qvy + d.z * qvz) * inv;
-        if (!(v >= 0.0f && u + v <= 1.0f)) continue;
-        const float t = (e2.x * qvx + e2.y * qvy + e2.z * qvz) * inv;
-        if (t > tmin && t < r.best) {
-            r.best = t;
-            r.bu = u;
-            r.bv = v;
-            r.best_tri = __float_as_uint(v0.w);
-            r.best_k = k;
-            if (ANY) {
-                r.t_hits = 0u;
-                r.g_hits = 0u;
-                r.sp = 0;
-                return;
-            }
+    const uint32_t b = __ffs(r.t_hits) - 1u;
+    r.t_hits &= r.t_hits - 1u;
+    const uint32_t k = r.t_base + __popc(r.t_all & ((1u << b) - 1u));
+    const float4 *tp = a.tris + 3 * (size_t)k;
+    const float4 v0 = __ldg(tp), e1 = __ldg(tp + 1), e2 = __ldg(tp + 2);
+    const float4 d = r.d, o = r.o;
+    const float pvx = d.y * e2.z - d.z * e2.y;
+    const float pvy = d.z * e2.x - d.x * e2.z;
+    const float pvz = d.x * e2.y - d.y * e2.x;
+    const float det = e1.x * pvx + e1.y * pvy + e1.z * pvz;
+    if (det == 0.0f) return;
+    const float inv = __frcp_rn(det);
+    const float tvx = o.x - v0.x, tvy = o.y - v0.y, tvz = o.z - v0.z;
+    const float u = (tvx * pvx + tvy * pvy + tvz * pvz) * inv;
+    if (!(u >= 0.0f && u <= 1.0f)) return;
+    const float qvx = tvy * e1.z - tvz * e1.y;
+    const float qvy = tvz * e1.x - tvx * e1.z;
+    const float qvz = tvx * e1.y - tvy * e1.x;
+    const float v = (d.x * qvx + d.y * qvy + d.z * qvz) * inv;
+    if (!(v >= 0.0f && u + v <= 1.0f)) return;
+    const float t = (e2.x * qvx + e2.y * qvy + e2.z * qvz) * inv;
+    if (t > tmin && t < r.best) {
+        r.best = t;
+        r.bu = u;
+        r.bv = v;
+        r.best_tri = __float_as_uint(v0.w);
+        r.best_k = k;
+        if (ANY) {
+            r.t_hits = 0u;
+            r.g_hits = 0u;
+            r.sp = 0;
         }
     }
 }
@@ -283,10 +281,6 @@ __device__ __forceinline__ float4 ray_result(const RayState &r, const SceneRef &
     const float tr = refine_t(a, r.best_k, r.o, r.d);
     return make_float4(isfinite(tr) ? tr : r.best, r.bu, r.bv, __uint_as_float(r.best_tri));
 }
-
-// Persistent warps: a warp takes kQueueBatch consecutive rays per queue fetch,
-// one per lane.
-constexpr uint32_t kQueueBatch = 32;
 
 // The length-table update of one traced ray (Section 3.1.6), the arithmetic of
 // table_accumulate_kernel: a ray that hit adds trunc(clamp(t*|d|/E, 0, 64)*2^24)
@@ -305,34 +299,43 @@ __device__ __forceinline__ void accumulate_hit(unsigned long long *table, const 
     atomicAdd(table + 2 * (size_t)cell + 1, 1ull);
 }
 
-// Traces ray i against the scene `sc` and writes its hit: the traversal loop
-// shared by every kernel variant.
+// One traversal step of a lane's ray: test one pending triangle, or (after
+// popping the next node group when the current one is used up) visit one
+// node.  Returns false once the ray is finished.  A stack that would
+// overflow records RR_DEVERR_TRACE_STACK and ends the ray as a miss.
 template <bool ANY>
-__device__ __forceinline__ float4 trace_ray(const SceneRef &sc, uint2 *stack, uint32_t *err, float4 o, float4 d) {
-    RayState r;
-    ray_begin(r, sc, o, d);
-    while (true) {
-        if (r.g_hits != 0u && !ray_visit_node(r, stack, sc)) {
-            atomicOr(err, RR_DEVERR_TRACE_STACK);
-            r.best_tri = kMiss;
-            break;
-        }
-        ray_test_triangles<ANY>(r, sc);
-        if (r.g_hits == 0u) {
-            if (r.sp == 0) break;
-            const uint2 e = stack[--r.sp];
-            r.g_base = e.x;
-            r.g_hits = e.y & 0xFFu;
-            r.g_imask = (e.y >> 8) & 0xFFu;
-        }
+__device__ __forceinline__ bool ray_step(RayState &r, uint2 *stack, const SceneRef &sc, uint32_t *err) {
+    if (r.t_hits != 0u) {
+        test_one_triangle<ANY>(r, sc);
+        return true;
     }
-    return ray_result(r, sc);
+    if (r.g_hits == 0u) {
+        if (r.sp == 0) return false;
+        const uint2 e = stack[--r.sp];
+        r.g_base = e.x;
+        r.g_hits = e.y & 0xFFu;
+        r.g_imask = (e.y >> 8) & 0xFFu;
+    }
+    if (!ray_visit_node(r, stack, sc)) {
+        atomicOr(err, RR_DEVERR_TRACE_STACK);
+        r.best_tri = kMiss;
+        r.g_hits = 0u;
+        r.t_hits = 0u;
+        r.sp = 0;
+    }
+    return true;
 }
 
-// Resident blocks asked of the compiler: 40 warps per SM (48 registers).
+// Lanes refill from the queue once this many of a warp's 32 lanes are idle
+// (their rays finished): finished lanes write their hits together and idle
+// lanes take consecutive queue positions together.
+constexpr uint32_t kRefillLanes = 8;
+
+// Resident blocks asked of the compiler: 32 warps per SM (64 registers: the
+// step loop keeps the ray's state and the refill bookkeeping without spills).
 template <int BLOCK>
 constexpr int trace_min_blocks() {
-    return 1280 / BLOCK > 0 ? 1280 / BLOCK : 1;
+    return 1024 / BLOCK > 0 ? 1024 / BLOCK : 1;
 }
 
 // Dynamic shared memory of the batch kernels: the scene of every segment, then
@@ -340,15 +343,22 @@ constexpr int trace_min_blocks() {
 inline size_t multi_smem(uint32_t n_segs) { return sizeof(SceneRef) * n_segs + sizeof(uint32_t) * (n_segs + 1); }
 
 // MULTI: rays of several scenes in one launch (a batch); each lane finds the
-// segment of its ray and traces that segment's BVH (and updates its table).
-// The segments' scenes sit in shared memory, so a lane keeps only its segment
-// number in registers during traversal.
+// segment of its ray when it takes the ray and traces that segment's BVH
+// (and updates its table).  The segments' scenes sit in shared memory, so a
+// lane keeps only its segment number in registers during traversal.
+//
+// Each lane traces its own ray, one traversal step (a node or a triangle) per
+// loop iteration, so a warp spends an iteration on triangle tests only for as
+// long as some lane has a triangle left, and lanes whose ray has finished are
+// refilled from the queue (kRefillLanes at a time) instead of idling until the
+// warp's slowest ray is done.
 template <bool ACCUM, bool ANY, bool MULTI, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, (trace_min_blocks<BLOCK>())) trace_kernel(TraceArgs a) {
     extern __shared__ __align__(16) unsigned char s_dyn[];
     SceneRef *s_sc = reinterpret_cast<SceneRef *>(s_dyn);
     uint32_t *s_off = reinterpret_cast<uint32_t *>(s_sc + (MULTI ? a.n_segs : 0));
     const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t lanes_below = (1u << lane) - 1u;
     // the table's quantisation frame is the same for the whole launch: it lives
     // in shared memory, not in every thread's registers during traversal
     __shared__ QuantFrame s_frame;
@@ -369,48 +379,67 @@ __global__ void __launch_bounds__(BLOCK, (trace_min_blocks<BLOCK>())) trace_kern
         }
     }
     if (MULTI || ACCUM) __syncthreads();
+    RayState r;
+    uint32_t ray = 0, seg = 0;
+    bool live = false, finished = false, exhausted = false;
     while (true) {
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(a.queue, kQueueBatch);
-        base = __shfl_sync(0xFFFFFFFFu, base, 0);
-        if (base >= a.n) break;
-#pragma unroll 1
-        for (uint32_t k = 0; k < kQueueBatch; k += 32) {
-            const uint32_t pos = base + k + lane;
-            if (pos >= a.n) break;
-            const uint32_t i = a.order ? __ldg(a.order + pos) : pos;
-            if (i >= a.n) {  // not a permutation of [0, n): record and skip
-                atomicOr(a.err, RR_DEVERR_BAD_INDEX);
-                continue;
-            }
-            const float4 o = __ldg(a.o_tmin + i), d = __ldg(a.d_tmax + i);
-            float4 h;
-            uint32_t seg = 0;
-            if (MULTI) {
-                // the last segment starting at or before i (empty segments share
-                // their start with the next one, which wins)
-                uint32_t lo = 0, hi = a.n_segs;
-                while (hi - lo > 1) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (s_off[mid] <= i)
-                        lo = mid;
-                    else
-                        hi = mid;
+        const uint32_t idle = __ballot_sync(0xFFFFFFFFu, !live);
+        if ((uint32_t)__popc(idle) >= kRefillLanes) {
+            if (finished) {  // the hits of the lanes whose rays finished
+                const SceneRef &sc = MULTI ? s_sc[seg] : a.scene;
+                const float4 h = ray_result(r, sc);
+                a.hits[ray] = h;
+                if (ACCUM) {
+                    if (MULTI) {
+                        const BatchScene *bs = a.segs + seg;
+                        if (bs->table) accumulate_hit(bs->table, bs->frame, bs->invE, r.o, r.d, h);
+                    } else if (a.table) {
+                        accumulate_hit(a.table, s_frame, s_invE, r.o, r.d, h);
+                    }
                 }
-                seg = lo;
-                h = trace_ray<ANY>(s_sc[seg], stack, a.err, o, d);
+                finished = false;
+            }
+            if (exhausted) {
+                if (idle == 0xFFFFFFFFu) break;
             } else {
-                h = trace_ray<ANY>(a.scene, stack, a.err, o, d);
-            }
-            a.hits[i] = h;
-            if (ACCUM) {
-                if (MULTI) {  // the segment's table and frame, read once the ray is done
-                    const BatchScene *bs = a.segs + seg;
-                    if (bs->table) accumulate_hit(bs->table, bs->frame, bs->invE, o, d, h);
-                } else if (a.table) {
-                    accumulate_hit(a.table, s_frame, s_invE, o, d, h);
+                // idle lanes take consecutive queue positions, in lane order
+                const uint32_t want = __popc(idle);
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(a.queue, want);
+                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                if (base + want >= a.n) exhausted = true;
+                if (!live) {
+                    const uint32_t pos = base + __popc(idle & lanes_below);
+                    if (pos < a.n) {
+                        const uint32_t i = a.order ? __ldg(a.order + pos) : pos;
+                        if (i >= a.n) {  // not a permutation of [0, n): record and skip
+                            atomicOr(a.err, RR_DEVERR_BAD_INDEX);
+                        } else {
+                            ray = i;
+                            if (MULTI) {
+                                // the last segment starting at or before i (empty
+                                // segments share their start with the next one, which wins)
+                                uint32_t lo = 0, hi = a.n_segs;
+                                while (hi - lo > 1) {
+                                    const uint32_t mid = (lo + hi) >> 1;
+                                    if (s_off[mid] <= i)
+                                        lo = mid;
+                                    else
+                                        hi = mid;
+                                }
+                                seg = lo;
+                            }
+                            ray_begin(r, MULTI ? s_sc[seg] : a.scene, __ldg(a.o_tmin + i), __ldg(a.d_tmax + i));
+                            live = true;
+                        }
+                    }
                 }
+                if (exhausted && __ballot_sync(0xFFFFFFFFu, live) == 0u) break;
             }
+        }
+        if (live && !ray_step<ANY>(r, stack, MULTI ? s_sc[seg] : a.scene, a.err)) {
+            live = false;
+            finished = true;
         }
     }
     __syncthreads();
@@ -530,7 +559,7 @@ int trace_blocks_per_sm(size_t smem) {
 template <bool ACC, bool ANY, bool MULTI, int BLOCK>
 void trace_enqueue(const TraceArgs &a, int sm_count, cudaStream_t s) {
     const size_t smem = MULTI ? multi_smem(a.n_segs) : 0;
-    const uint32_t want = (a.n + kQueueBatch - 1) / kQueueBatch;  // warps that can get work
+    const uint32_t want = (a.n + 31u) / 32u;  // warps that can get work
     uint32_t grid = (uint32_t)sm_count * (uint32_t)trace_blocks_per_sm<ACC, ANY, MULTI, BLOCK>(smem);
     grid = std::max(1u, std::min(grid, (want + BLOCK / 32 - 1) / (BLOCK / 32)));
     trace_kernel<ACC, ANY, MULTI, BLOCK><<<grid, BLOCK, smem, s>>>(a);
