@@ -228,6 +228,25 @@ def test_sort_long_passes_match_oracle(radix_bits, bits):
     assert_no_device_error()
 
 
+@pytest.mark.parametrize("radix_bits", [8, 4])
+@pytest.mark.parametrize("bits", [32, 64])
+def test_sort_one_and_two_wave_passes_match_oracle(radix_bits, bits):
+    """Digit passes of just under and just over one and two full waves of
+    three blocks per SM (a tile's look-back then waits on tiles that start
+    later), with a ragged last tile and repeated keys, against the oracle."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    tile = 256 * (12 if bits > 32 else 16)
+    rng = np.random.default_rng(99 + bits + radix_bits)
+    for tiles in (3 * sms - 1, 3 * sms + 1, 6 * sms - 1, 6 * sms + 1):
+        n = (tiles - 1) * tile + 7
+        keys = _random_keys(n, bits, rng, dup=tiles % 2 == 1)
+        perm_or, sk_or = oracle.stable_sort(keys)
+        perm, sk = gpu_sort(keys, bits, radix_bits)
+        assert np.array_equal(perm, perm_or), (tiles, n)
+        assert np.array_equal(sk, sk_or), (tiles, n)
+    assert_no_device_error()
+
+
 @pytest.mark.parametrize("bits", [32, 64])
 def test_sort_without_key_output_and_determinism(bits):
     rng = np.random.default_rng(5)
