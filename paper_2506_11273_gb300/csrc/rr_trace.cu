@@ -599,9 +599,22 @@ rr_status launch_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax
         a.tlo[c] = table ? table->box.lo[c] : 0.0f;
         a.thi[c] = table ? table->box.hi[c] : 0.0f;
     }
-    return with_trace_queue(ds, s, [&](uint32_t *queue) {
+    // The length-table update: a separate pass over the traced rays when the
+    // hits land in device memory (it runs at full lane use, with lanes that
+    // share a cell combined before the atomics, and reads rays and hits from
+    // L2), fused into the trace when they go straight to host memory.
+    cudaPointerAttributes pa{};
+    bool hits_on_device = false;
+    if (table) {
+        if (cudaPointerGetAttributes(&pa, hits_out) == cudaSuccess)
+            hits_on_device = pa.type == cudaMemoryTypeDevice;
+        else
+            cudaGetLastError();
+    }
+    const bool fuse = table && !hits_on_device;
+    const rr_status st2 = with_trace_queue(ds, s, [&](uint32_t *queue) {
         a.queue = queue;
-        if (table)
+        if (fuse)
             trace_enqueue<true, false, false, kTraceBlock>(a, ds->sm_count, s);
         else if (any)
             trace_enqueue<false, true, false, kTraceBlock>(a, ds->sm_count, s);
@@ -610,6 +623,8 @@ rr_status launch_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax
         note_launches(1);
         return check_launch(what);
     });
+    if (st2 != RR_OK || !table || fuse) return st2;
+    return rr_length_table_accumulate(table, o_tmin, d_tmax, hits_out, n, stream);
 }
 
 }  // namespace
