@@ -940,11 +940,18 @@ def bench_serving(args, dev, slots: int = 4, max_batch_rays: int = 1 << 23, frac
             o, d = pools[(int(which[k]), str(kinds[k]))]
             tickets.append((srv.submit(int(which[k]), o, d, hits_sink, n=int(sizes[k])), int(sizes[k])))
         lat, queued, service, rays, first, last = [], [], [], 0, None, None
+        parts = {"enqueue": [], "device": [], "copy_in": [], "kernels": [], "copy_out": [], "device_start_and_host_fn": []}
         for t, n in tickets:
             tm = srv.wait(t)
             lat.append((tm["done_ns"] - tm["submit_ns"]) * 1e-6)
             queued.append((tm["start_ns"] - tm["submit_ns"]) * 1e-6)
             service.append((tm["done_ns"] - tm["start_ns"]) * 1e-6)
+            parts["enqueue"].append((tm["enqueued_ns"] - tm["start_ns"]) * 1e-6)
+            parts["device"].append(tm["device_ms"])
+            parts["copy_in"].append(tm["copy_in_ms"])
+            parts["kernels"].append(tm["kernels_ms"])
+            parts["copy_out"].append(tm["copy_out_ms"])
+            parts["device_start_and_host_fn"].append((tm["done_ns"] - tm["enqueued_ns"]) * 1e-6 - tm["device_ms"])
             rays += n
             first = tm["submit_ns"] if first is None else min(first, tm["submit_ns"])
             last = tm["done_ns"] if last is None else max(last, tm["done_ns"])
@@ -955,6 +962,8 @@ def bench_serving(args, dev, slots: int = 4, max_batch_rays: int = 1 << 23, frac
                 "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(lat.mean()), 3),
                 "queued_p50_p99_ms": [round(float(np.percentile(queued, q)), 3) for q in (50, 99)],
                 "in_batch_p50_p99_ms": [round(float(np.percentile(service, q)), 3) for q in (50, 99)],
+                "in_batch_split_p50_p99_ms": {k: [round(float(np.percentile(v, q)), 3) for q in (50, 99)]
+                                              for k, v in parts.items()},
                 "throughput_mrays": round(rays / span / 1e6, 1)}
 
     # capacity: bursts of 256 requests submitted at once (the better of two),
@@ -976,6 +985,7 @@ def bench_serving(args, dev, slots: int = 4, max_batch_rays: int = 1 << 23, frac
                                                    SERVE_BUDGET >> 30, slots, max(max_batch_rays, hi_n)),
             "capacity_mrays": cap_mrays, "loads": loads, "setup_s": round(setup_s, 1),
             "batches": st["batches"], "max_batch_requests": st["max_batch_requests"],
+            "engine_slowdowns": st["engine_slowdowns"], "kernel_copy_groups": st["kernel_copy_groups"],
             "clocks": clk.summary(),
             "pool_h2d_result_d2h_gbs": link_before,
             "peak_reserved_gb": round(st["peak_reserved_bytes"] / 2**30, 2)}

@@ -521,7 +521,14 @@ typedef struct {
     uint64_t reserve_bytes;    /* device memory taken from the pool and returned at creation, so
                                   that the first groups do not wait for the pool to grow (0: none;
                                   at most budget_bytes) */
+    uint32_t upload;           /* how page-locked request rays go up: RR_UPLOAD_ADAPTIVE (0),
+                                  RR_UPLOAD_ENGINES (1) or RR_UPLOAD_KERNEL (2) */
 } rr_server_config;
+
+/* Upload policies of rr_server_config.upload (see rr_server_submit). */
+#define RR_UPLOAD_ADAPTIVE 0u /* copy engines; the copy kernel for 10 s after a slow engine upload */
+#define RR_UPLOAD_ENGINES 1u  /* always the copy engines */
+#define RR_UPLOAD_KERNEL 2u   /* always the library's copy kernel (page-locked, 16-byte aligned rays) */
 
 typedef struct {
     uint64_t submit_ns;        /* steady-clock times: submission, */
@@ -531,6 +538,12 @@ typedef struct {
     uint32_t device_flags;     /* RR_DEVERR_* flags the group's kernels recorded (0: none); when
                                   non-zero rr_server_wait returns RR_ERR_DEVICE for each request of
                                   that group, and requests of other groups are unaffected */
+    uint64_t enqueued_ns;      /* steady-clock time the group's work was fully enqueued */
+    float copy_in_ms;          /* device time of the group's stages (CUDA events on its stream): */
+    float kernels_ms;          /*   rays up, keys + sort + trace, hits down */
+    float copy_out_ms;
+    float device_ms;           /* from the group's first copy to its last, waits on the device included */
+    uint32_t kernel_copies;    /* 1: the group's page-locked rays were uploaded by the copy kernel */
 } rr_request_times;
 
 typedef struct {
@@ -539,6 +552,8 @@ typedef struct {
     uint64_t peak_reserved_bytes; /* most device memory admitted at once */
     uint64_t reserved_bytes;      /* device memory admitted now */
     uint64_t waiting;             /* requests not yet admitted */
+    uint64_t engine_slowdowns;    /* slow copy-engine uploads seen (each moves uploads to the copy kernel for 10 s) */
+    uint64_t kernel_copy_groups;  /* groups whose page-locked rays were uploaded by the copy kernel */
 } rr_server_stats_t;
 
 typedef struct rr_server rr_server;
@@ -562,9 +577,15 @@ rr_status rr_server_add_scene(rr_server *srv, const rr_bvh *bvh, rr_length_table
 /*
  * Queues a request of n rays (host float4 o_tmin and d_tmax; hits_host
  * receives n float4 hits in input order).  The buffers must stay valid and
- * untouched until rr_server_wait returns for the ticket; pinned host memory
- * lets the copies run asynchronously.  Returns at once.  A request whose
- * memory alone exceeds the budget is refused (RR_ERR_INVALID_ARG).
+ * untouched until rr_server_wait returns for the ticket.  Page-locked buffers
+ * (cudaHostAlloc / cudaHostRegister) let the copies run asynchronously; rays
+ * go up through the copy engines unless an upload of the last 10 s ran below
+ * 40 GB/s, in which case page-locked, 16-byte aligned rays are uploaded by the
+ * library's copy kernel (SM loads over the host link).  On
+ * GB300 the copy engines were measured to slow down to 11-20 GB/s for ~70 ms
+ * every ~0.5 s after an earlier process had used the GPU, while kernel copies
+ * kept ~207 GB/s.  Returns at once.  A request whose memory alone exceeds the
+ * budget is refused (RR_ERR_INVALID_ARG).
  */
 rr_status rr_server_submit(rr_server *srv, uint32_t scene_id, const float *o_tmin_host,
                            const float *d_tmax_host, uint32_t n, float *hits_host, uint64_t *ticket);

@@ -1,5 +1,6 @@
 // Library-wide plumbing: status strings, per-thread error messages, the
 // per-device error word and launch accounting.
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 
@@ -152,6 +153,51 @@ rr_status enqueue_take_error(uint32_t *word, uint32_t *out, cudaStream_t s) {
     take_error_kernel<<<1, 1, 0, s>>>(word, out);
     note_launches(1);
     return check_launch("device error word");
+}
+
+void *mapped_host_range(const void *host, size_t bytes) {
+    if (!host || bytes == 0) return nullptr;
+    cudaPointerAttributes a{}, b{};
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess ||
+        cudaPointerGetAttributes(&b, static_cast<const char *>(host) + bytes - 1) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+        return nullptr;
+    if (static_cast<char *>(b.devicePointer) - static_cast<char *>(a.devicePointer) != (ptrdiff_t)(bytes - 1))
+        return nullptr;
+    return a.devicePointer;
+}
+
+namespace {
+// Eight 16-byte words per thread per round, strided over the grid: one block
+// per SM keeps 32 KB of host-link reads in flight, enough for the link's
+// rate while taking few warp slots from kernels running beside it.
+constexpr int kCopyDepth = 8;
+__global__ void __launch_bounds__(256) kernel_copy_kernel(const uint4 *__restrict__ src, uint4 *__restrict__ dst,
+                                                         size_t n16) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (kCopyDepth - 1) * stride < n16; i += kCopyDepth * stride) {
+        uint4 v[kCopyDepth];
+#pragma unroll
+        for (int k = 0; k < kCopyDepth; ++k) v[k] = src[i + k * stride];
+#pragma unroll
+        for (int k = 0; k < kCopyDepth; ++k) dst[i + k * stride] = v[k];
+    }
+    for (; i < n16; i += stride) dst[i] = src[i];
+}
+}  // namespace
+
+rr_status enqueue_kernel_copy(void *dst, const void *src, size_t bytes, int sm_count, cudaStream_t s) {
+    if (bytes == 0) return RR_OK;
+    const size_t n16 = bytes / 16;
+    const size_t want = (n16 + 256 * kCopyDepth - 1) / (256 * kCopyDepth);  // blocks that each get a full round
+    const uint32_t blocks = (uint32_t)std::max<size_t>(1, std::min<size_t>(want, (size_t)sm_count));
+    kernel_copy_kernel<<<blocks, 256, 0, s>>>(static_cast<const uint4 *>(src), static_cast<uint4 *>(dst), n16);
+    note_launches(1);
+    return check_launch("host-link copy");
 }
 }  // namespace rr
 

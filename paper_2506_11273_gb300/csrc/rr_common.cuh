@@ -71,6 +71,16 @@ uint32_t take_noalloc_error();
 // device-accessible (device or page-locked host memory).
 rr_status enqueue_take_error(uint32_t *word, uint32_t *out, cudaStream_t s);
 
+// Device address of the page-locked host range [host, host + bytes), or null
+// when either end is not page-locked, mapped host memory.
+void *mapped_host_range(const void *host, size_t bytes);
+
+// Copies `bytes` (a multiple of 16) between two device-accessible addresses
+// (device memory or page-locked host memory) with a kernel: SM loads and
+// stores over the host link instead of the copy engines, which the driver
+// may be using for its own work.  Enqueued on `s`.
+rr_status enqueue_kernel_copy(void *dst, const void *src, size_t bytes, int sm_count, cudaStream_t s);
+
 // Counts kernel launches made by the library.
 void note_launches(uint32_t k);
 

@@ -41,6 +41,9 @@ struct Request {
     uint32_t scene;
     const float *o, *d;
     float *hits;
+    // device addresses of the rays when they are page-locked host memory (then
+    // they may be uploaded by the library's copy kernel), else null
+    const float *o_dev = nullptr, *d_dev = nullptr;
     uint32_t n;
     rr_request_times times;
     rr_status status = RR_OK;
@@ -54,6 +57,7 @@ struct Slot {
     uint32_t *queue = nullptr;       // trace work-queue words of this slot
     uint32_t *err = nullptr;         // device error word of the slot's stream
     uint32_t *h_err = nullptr;       // pinned: the flags of the slot's last group, read after its copy-out
+    cudaEvent_t ev[4] = {};          // the group's stages: before copy-in, after it, after the trace, after copy-out
     BatchScene *h_segs = nullptr;    // pinned staging of the group's descriptors
     uint32_t *h_offs = nullptr;      // and offsets (one group in flight per slot)
     Group *busy = nullptr;
@@ -63,8 +67,22 @@ struct Group {
     rr_server *server = nullptr;
     uint32_t slot = 0;
     std::vector<Request *> reqs;
-    size_t bytes = 0;  // charged against the budget
+    size_t bytes = 0;    // charged against the budget
+    bool timed = false;  // the slot's stage events were all recorded for this group
+    bool kernel_copies = false;  // page-locked rays uploaded by the library's copy kernel
+    uint64_t engine_bytes = 0;   // bytes uploaded by the copy engines
 };
+
+// Uploads of page-locked request rays normally go through the copy engines,
+// which overlap other groups' kernels at no cost in SM time.  On GB300 the
+// engines were measured to slow down to 11-20 GB/s for ~70 ms every ~0.5 s
+// after an earlier process had used the GPU; a group whose engine upload runs
+// below kSlowEngineGBs therefore switches uploads to the copy kernel (SM loads
+// over the host link, unaffected) for kKernelCopyNs (the slowdowns persist
+// for minutes once they start), after which the engines are tried again.
+constexpr double kSlowEngineGBs = 40.0;
+constexpr uint64_t kMinTimedUpload = 16ull << 20;
+constexpr uint64_t kKernelCopyNs = 10000000000ull;
 
 }  // namespace
 
@@ -86,6 +104,8 @@ struct rr_server {
     uint64_t batches = 0, max_group = 0, peak_reserved = 0;
     std::string worker_error;
     int sm_count = 0;
+    uint64_t kernel_copies_until = 0;  // steady-clock ns: uploads by the copy kernel until then
+    uint64_t engine_slowdowns = 0, kernel_copy_groups = 0;
 };
 
 namespace {
@@ -139,7 +159,8 @@ rr_status launch_group(rr_server *s, Group *g) {
     size_t ws = 0;
     rr_sort_workspace_size((uint32_t)std::max<uint64_t>(n, 1), total_bits, s->cfg.radix_bits, &ws);
     unsigned char *mem = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&mem), g->bytes, st);
+    cudaError_t e = cudaEventRecord(sl.ev[0], st);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&mem), g->bytes, st);
     if (e != cudaSuccess) return fail_cuda(e, "rr_server: cudaMallocAsync");
     size_t off = 0;
     float *o = reinterpret_cast<float *>(mem + off);
@@ -158,15 +179,27 @@ rr_status launch_group(rr_server *s, Group *g) {
     off += up256(sizeof(BatchScene) * ng);
     uint32_t *offs = reinterpret_cast<uint32_t *>(mem + off);
     uint64_t at = 0;
-    for (uint32_t k = 0; k < ng && e == cudaSuccess; ++k) {
+    rr_status cs = RR_OK;
+    for (uint32_t k = 0; k < ng && e == cudaSuccess && cs == RR_OK; ++k) {
         Request *r = g->reqs[k];
-        e = cudaMemcpyAsync(o + 4 * at, r->o, 16ull * r->n, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d + 4 * at, r->d, 16ull * r->n, cudaMemcpyHostToDevice, st);
+        if (!(g->kernel_copies && r->o_dev && r->d_dev)) g->engine_bytes += 32ull * r->n;
+        if (g->kernel_copies && r->o_dev && r->d_dev) {
+            cs = enqueue_kernel_copy(o + 4 * at, r->o_dev, 16ull * r->n, s->sm_count, st);
+            if (cs == RR_OK) cs = enqueue_kernel_copy(d + 4 * at, r->d_dev, 16ull * r->n, s->sm_count, st);
+        } else {
+            e = cudaMemcpyAsync(o + 4 * at, r->o, 16ull * r->n, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d + 4 * at, r->d, 16ull * r->n, cudaMemcpyHostToDevice, st);
+        }
         at += r->n;
+    }
+    if (cs != RR_OK) {
+        cudaFreeAsync(mem, st);
+        return cs;
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(segs, sl.h_segs, sizeof(BatchScene) * ng, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(offs, sl.h_offs, 4ull * (ng + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.ev[1], st);
     if (e != cudaSuccess) {
         cudaFreeAsync(mem, st);
         return fail_cuda(e, "rr_server: copy-in");
@@ -182,6 +215,7 @@ rr_status launch_group(rr_server *s, Group *g) {
             rs = launch_trace_batch(segs, offs, ng, o, d, perm, (uint32_t)n, hits, adaptive(s),
                                     s->cfg.trace_block, sl.queue, sl.err, st);
     }
+    if (rs == RR_OK) e = cudaEventRecord(sl.ev[2], st);
     at = 0;
     for (uint32_t k = 0; k < ng && rs == RR_OK && e == cudaSuccess; ++k) {
         Request *r = g->reqs[k];
@@ -193,6 +227,8 @@ rr_status launch_group(rr_server *s, Group *g) {
     if (e != cudaSuccess) return fail_cuda(e, "rr_server: copy-out");
     rs = enqueue_take_error(sl.err, sl.h_err, st);
     if (rs != RR_OK) return rs;
+    e = cudaEventRecord(sl.ev[3], st);
+    if (e != cudaSuccess) return fail_cuda(e, "rr_server: event");
     e = cudaLaunchHostFunc(st, group_done, g);
     if (e != cudaSuccess) return fail_cuda(e, "rr_server: host function");
     return RR_OK;
@@ -204,6 +240,29 @@ void worker_main(rr_server *s) {
     while (true) {
         // retire finished groups: release their memory and slots
         for (Group *g : s->finished) {
+            // the device time of the group's stages (its events have completed)
+            const Slot &sl = s->slots[g->slot];
+            float t[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            if (g->timed && cudaEventElapsedTime(&t[0], sl.ev[0], sl.ev[1]) == cudaSuccess &&
+                cudaEventElapsedTime(&t[1], sl.ev[1], sl.ev[2]) == cudaSuccess &&
+                cudaEventElapsedTime(&t[2], sl.ev[2], sl.ev[3]) == cudaSuccess &&
+                cudaEventElapsedTime(&t[3], sl.ev[0], sl.ev[3]) == cudaSuccess) {
+                for (Request *r : g->reqs) {
+                    r->times.copy_in_ms = t[0];
+                    r->times.kernels_ms = t[1];
+                    r->times.copy_out_ms = t[2];
+                    r->times.device_ms = t[3];
+                    r->times.kernel_copies = g->kernel_copies ? 1u : 0u;
+                }
+                // a slow engine upload moves the next uploads to the copy kernel
+                if (!g->kernel_copies && g->engine_bytes >= kMinTimedUpload && t[0] > 0.0f &&
+                    (double)g->engine_bytes / (t[0] * 1e6) < kSlowEngineGBs) {
+                    s->kernel_copies_until = now_ns() + kKernelCopyNs;
+                    ++s->engine_slowdowns;
+                }
+            } else {
+                cudaGetLastError();
+            }
             for (Request *r : g->reqs) r->done = true;
             s->reserved -= g->bytes;
             s->slots[g->slot].busy = nullptr;
@@ -227,6 +286,9 @@ void worker_main(rr_server *s) {
             Group *g = new Group();
             g->server = s;
             g->slot = (uint32_t)free_slot;
+            g->kernel_copies = s->cfg.upload == RR_UPLOAD_KERNEL ||
+                               (s->cfg.upload == RR_UPLOAD_ADAPTIVE && now_ns() < s->kernel_copies_until);
+            if (g->kernel_copies) ++s->kernel_copy_groups;
             uint64_t n = 0;
             while (!s->waiting.empty() && g->reqs.size() < kMaxBatchSegments) {
                 Request *r = s->waiting.front();
@@ -262,7 +324,10 @@ void worker_main(rr_server *s) {
                 sl.h_offs[ng] = (uint32_t)at;
                 lock.unlock();
                 const rr_status st = launch_group(s, g);
+                const uint64_t t_enq = now_ns();
                 lock.lock();
+                g->timed = st == RR_OK;
+                for (Request *r : g->reqs) r->times.enqueued_ns = t_enq;
                 if (st != RR_OK) {
                     s->worker_error = rr_last_error_message();
                     for (Request *r : g->reqs) {
@@ -299,6 +364,7 @@ extern "C" rr_status rr_server_create(const rr_server_config *cfg, rr_server **o
         return fail(RR_ERR_INVALID_ARG, "rr_server_create: bad t_source");
     if (cfg->max_batch_rays < 1 || cfg->max_batch_rays >= (1u << 30))
         return fail(RR_ERR_INVALID_ARG, "rr_server_create: max_batch_rays must be 1..2^30-1");
+    if (cfg->upload > RR_UPLOAD_KERNEL) return fail(RR_ERR_INVALID_ARG, "rr_server_create: unknown upload policy");
     rr_status st;
     DeviceState *ds = device_state(&st);
     if (!ds) return st;
@@ -313,6 +379,8 @@ extern "C" rr_status rr_server_create(const rr_server_config *cfg, rr_server **o
         if (e == cudaSuccess) sl.err = error_word(ds, sl.stream);
         if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&sl.h_err), sizeof(uint32_t));
         if (e == cudaSuccess) *sl.h_err = 0u;
+        for (cudaEvent_t &ev : sl.ev)
+            if (e == cudaSuccess) e = cudaEventCreate(&ev);
         if (e == cudaSuccess) e = cudaMalloc(&sl.queue, 2 * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMemset(sl.queue, 0, 2 * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&sl.h_segs), sizeof(BatchScene) * kMaxBatchSegments);
@@ -340,6 +408,8 @@ extern "C" rr_status rr_server_create(const rr_server_config *cfg, rr_server **o
             cudaFreeHost(sl.h_segs);
             cudaFreeHost(sl.h_offs);
             cudaFreeHost(sl.h_err);
+            for (cudaEvent_t ev : sl.ev)
+                if (ev) cudaEventDestroy(ev);
         }
         delete s;
         return fail_cuda(e, "rr_server_create");
@@ -400,6 +470,11 @@ extern "C" rr_status rr_server_submit(rr_server *s, uint32_t scene_id, const flo
     r->d = d_tmax_host;
     r->hits = hits_host;
     r->n = n;
+    if (n > 0) {
+        r->o_dev = static_cast<const float *>(mapped_host_range(o_tmin_host, 16ull * n));
+        r->d_dev = static_cast<const float *>(mapped_host_range(d_tmax_host, 16ull * n));
+        if (!aligned16(r->o_dev) || !aligned16(r->d_dev)) r->o_dev = r->d_dev = nullptr;
+    }
     r->times = rr_request_times{};
     std::lock_guard<std::mutex> lock(s->mu);
     if (scene_id >= s->scenes.size()) {
@@ -448,6 +523,8 @@ extern "C" rr_status rr_server_stats(rr_server *s, rr_server_stats_t *out) {
     out->peak_reserved_bytes = s->peak_reserved;
     out->reserved_bytes = s->reserved;
     out->waiting = s->waiting.size();
+    out->engine_slowdowns = s->engine_slowdowns;
+    out->kernel_copy_groups = s->kernel_copy_groups;
     return RR_OK;
 }
 
@@ -466,6 +543,8 @@ extern "C" rr_status rr_server_destroy(rr_server *s) {
         cudaFreeHost(sl.h_segs);
         cudaFreeHost(sl.h_offs);
         cudaFreeHost(sl.h_err);
+        for (cudaEvent_t ev : sl.ev)
+            if (ev) cudaEventDestroy(ev);
     }
     for (auto &kv : s->all) delete kv.second;
     delete s;

@@ -33,6 +33,7 @@ RR_DEVERR_TRACE_STACK = 0x2
 RR_DEVERR_BAD_INDEX = 0x4
 RR_DEVERR_COPY_TIMEOUT = 0x8
 RR_TRACE_ANY_HIT = 0x1
+RR_UPLOAD_ADAPTIVE, RR_UPLOAD_ENGINES, RR_UPLOAD_KERNEL = 0, 1, 2
 MISS = 0xFFFFFFFF
 TABLE_CELLS = 1 << 20
 
@@ -86,17 +87,20 @@ class ServerConfig(C.Structure):
     _fields_ = [("budget_bytes", C.c_uint64), ("slots", C.c_uint32), ("max_batch_rays", C.c_uint32),
                 ("layout", C.c_uint32), ("t_source", C.c_uint32), ("ratio", C.c_float),
                 ("key_bits", C.c_uint32), ("radix_bits", C.c_uint32), ("trace_block", C.c_uint32),
-                ("reserve_bytes", C.c_uint64)]
+                ("reserve_bytes", C.c_uint64), ("upload", C.c_uint32)]
 
 
 class RequestTimes(C.Structure):
     _fields_ = [("submit_ns", C.c_uint64), ("start_ns", C.c_uint64), ("done_ns", C.c_uint64),
-                ("batch_requests", C.c_uint32), ("device_flags", C.c_uint32)]
+                ("batch_requests", C.c_uint32), ("device_flags", C.c_uint32), ("enqueued_ns", C.c_uint64),
+                ("copy_in_ms", C.c_float), ("kernels_ms", C.c_float), ("copy_out_ms", C.c_float),
+                ("device_ms", C.c_float), ("kernel_copies", C.c_uint32)]
 
 
 class ServerStats(C.Structure):
     _fields_ = [("batches", C.c_uint64), ("max_batch_requests", C.c_uint64),
-                ("peak_reserved_bytes", C.c_uint64), ("reserved_bytes", C.c_uint64), ("waiting", C.c_uint64)]
+                ("peak_reserved_bytes", C.c_uint64), ("reserved_bytes", C.c_uint64), ("waiting", C.c_uint64),
+                ("engine_slowdowns", C.c_uint64), ("kernel_copy_groups", C.c_uint64)]
 
 
 class BvhInfo(C.Structure):
@@ -511,9 +515,10 @@ class Server:
 
     def __init__(self, budget_bytes: int, slots: int = 4, max_batch_rays: int = 1 << 24,
                  layout: int = RR_KEY_TWO_POINT, t_source: int = RR_T_FIXED, ratio: float = 0.25,
-                 key_bits: int = 24, radix_bits: int = 8, trace_block: int = 256, reserve_bytes: int = 0):
+                 key_bits: int = 24, radix_bits: int = 8, trace_block: int = 256, reserve_bytes: int = 0,
+                 upload: int = 0):
         cfg = ServerConfig(int(budget_bytes), slots, max_batch_rays, layout, t_source, float(np.float32(ratio)),
-                           key_bits, radix_bits, trace_block, int(reserve_bytes))
+                           key_bits, radix_bits, trace_block, int(reserve_bytes), int(upload))
         h = C.c_void_p()
         _check(lib().rr_server_create(C.byref(cfg), C.byref(h)), "rr_server_create")
         self.handle = h
@@ -551,8 +556,7 @@ class Server:
         tm = RequestTimes()
         _check(lib().rr_server_wait(self.handle, ticket, timeout_s, C.byref(tm)), "rr_server_wait")
         self._held.pop(ticket, None)
-        return dict(submit_ns=tm.submit_ns, start_ns=tm.start_ns, done_ns=tm.done_ns,
-                    batch_requests=tm.batch_requests, device_flags=tm.device_flags)
+        return {k: getattr(tm, k) for k, _ in RequestTimes._fields_}
 
     def stats(self) -> dict:
         st = ServerStats()

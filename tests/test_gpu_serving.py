@@ -35,9 +35,10 @@ def scenes():
     return tris, [rr.BVH(t) for t in tris], [W.scene_aabb(t) for t in tris], reqs
 
 
-def _server(scenes, budget, slots, tsrc=rr.RR_T_FIXED, tables=None):
+def _server(scenes, budget, slots, tsrc=rr.RR_T_FIXED, tables=None, upload=rr.RR_UPLOAD_ADAPTIVE):
     tris, bvhs, boxes, _ = scenes
-    srv = rr.Server(budget_bytes=budget, slots=slots, max_batch_rays=1 << 20, t_source=tsrc, key_bits=32)
+    srv = rr.Server(budget_bytes=budget, slots=slots, max_batch_rays=1 << 20, t_source=tsrc, key_bits=32,
+                    upload=upload)
     for s in range(3):
         sid = srv.add_scene(bvhs[s], boxes[s][0], boxes[s][1], tables[s] if tables else None)
         assert sid == s
@@ -97,28 +98,43 @@ def test_results_same_alone_and_in_the_mix(scenes, adaptive):
 
 def test_requests_arriving_while_others_run(scenes):
     """Submissions interleaved with waits: later requests join while earlier
-    groups are on the device; pinned host tensors as buffers."""
+    groups are on the device; pinned host tensors as buffers.  The rays go up
+    through the copy engines, through the library's copy kernel, and by the
+    adaptive choice: the hits are the same bit for bit and correct."""
     tris, bvhs, boxes, reqs = scenes
-    srv = _server(scenes, budget=64 << 20, slots=2)
     pinned = []
     for s, r in reqs:
         o = torch.from_numpy(r.o_tmin).pin_memory()
         d = torch.from_numpy(r.d_tmax).pin_memory()
-        h = torch.zeros(r.o_tmin.shape[0], 4).pin_memory()
-        pinned.append((s, o, d, h))
-    tickets = []
-    for k, (s, o, d, h) in enumerate(pinned):
-        tickets.append(srv.submit(s, o, d, h))
-        if k % 4 == 3:
-            srv.wait(tickets[k - 2])
-            tickets[k - 2] = None
-    for t in tickets:
-        if t is not None:
-            srv.wait(t)
-    srv.close()
-    for (s, r), (_, _, _, h) in zip(reqs, pinned):
+        pinned.append((s, o, d))
+    results = {}
+    for upload in (rr.RR_UPLOAD_ENGINES, rr.RR_UPLOAD_KERNEL, rr.RR_UPLOAD_ADAPTIVE):
+        srv = _server(scenes, budget=64 << 20, slots=2, upload=upload)
+        hits = [torch.zeros(o.shape[0], 4).pin_memory() for _, o, _ in pinned]
+        tickets, modes = [], []
+        for k, ((s, o, d), h) in enumerate(zip(pinned, hits)):
+            tickets.append(srv.submit(s, o, d, h))
+            if k % 4 == 3:
+                modes.append(srv.wait(tickets[k - 2])["kernel_copies"])
+                tickets[k - 2] = None
+        for t in tickets:
+            if t is not None:
+                modes.append(srv.wait(t)["kernel_copies"])
+        st = srv.stats()
+        srv.close()
+        if upload == rr.RR_UPLOAD_ENGINES:
+            assert set(modes) == {0} and st["kernel_copy_groups"] == 0
+        elif upload == rr.RR_UPLOAD_KERNEL:
+            assert set(modes) == {1} and st["kernel_copy_groups"] == st["batches"]
+        results[upload] = [h.numpy().copy() for h in hits]
+    for upload in (rr.RR_UPLOAD_KERNEL, rr.RR_UPLOAD_ADAPTIVE):
+        for a, b in zip(results[rr.RR_UPLOAD_ENGINES], results[upload]):
+            assert np.array_equal(_bits(a), _bits(b))
+    for (s, r), h in zip(reqs, results[rr.RR_UPLOAD_KERNEL]):
         oh, oi = oracle.BVH(tris[s]).trace(r.o_tmin, r.d_tmax)
-        compare(tris[s], r.o_tmin, r.d_tmax, h.numpy(), oh, oi)
+        compare(tris[s], r.o_tmin, r.d_tmax, h, oh, oi)
+    with pytest.raises(rr.RRError):  # unknown policy
+        rr.Server(budget_bytes=1 << 20, upload=3)
     assert rr.rr_device_error() == 0
 
 
