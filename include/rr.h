@@ -629,6 +629,24 @@ rr_status rr_selftest_lookback_timeout(void *stream);
  */
 rr_status rr_stream_error(void *stream, uint32_t *flags_out);
 
+/*
+ * rr_fault_inject - host-side fault injection for testing callers' error paths
+ * (no paper counterpart).  spec "alloc@N", "launch@N" or "timeout@N" (N >= 1)
+ * makes the N-th event of that kind from now on fail, once:
+ *   alloc    a device allocation owned by the library (handles, the serving
+ *            loop's group memory) fails as cudaMalloc would: RR_ERR_OOM or
+ *            RR_ERR_CUDA from the call, or the request's status for a served
+ *            group; nothing of that allocation's work is enqueued;
+ *   launch   a launch check reports RR_ERR_CUDA (the kernels of that call may
+ *            have been enqueued; its outputs are undefined);
+ *   timeout  rr_server_wait or rr_pipeline_wait returns RR_ERR_TIMEOUT at once
+ *            without waiting; the ticket stays valid and can be waited on again.
+ * NULL or "" clears.  The environment variable RR_FAULT sets a spec at load
+ * time.  No GPU fault is ever made; handles stay usable after an injected
+ * failure.  A malformed spec returns RR_ERR_INVALID_ARG.
+ */
+rr_status rr_fault_inject(const char *spec);
+
 /* Synchronises the device, then reads and clears every stream's error word and
  * the error word of rr_sort_noalloc, returning the union of their flags. */
 rr_status rr_device_error(uint32_t *flags_out);

@@ -2,6 +2,7 @@
 // per-device error word and launch accounting.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <mutex>
 
 #include "rr_common.cuh"
@@ -30,7 +31,69 @@ void note_launches(uint32_t k) { g_launches.fetch_add(k, std::memory_order_relax
 rr_status check_launch(const char *what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail_cuda(e, what);
+    if (fault_fires(Fault::Launch)) return fail(RR_ERR_CUDA, std::string(what) + ": injected launch failure");
     return RR_OK;
+}
+
+// ------------------------------------------------------------------ fault injection
+
+static std::atomic<int> g_fault_kind{0};
+static std::atomic<long long> g_fault_left{0};
+static std::once_flag g_fault_env;
+
+// Parses "alloc@N", "launch@N" or "timeout@N" (N >= 1); "" clears.
+static bool parse_fault(const char *spec, int *kind, long long *n) {
+    *kind = 0;
+    *n = 0;
+    if (!spec || !*spec) return true;
+    const std::string s(spec);
+    const size_t at = s.find('@');
+    if (at == std::string::npos) return false;
+    const std::string k = s.substr(0, at), num = s.substr(at + 1);
+    if (num.empty() || num.size() > 12 || num.find_first_not_of("0123456789") != std::string::npos) return false;
+    const long long v = std::stoll(num);
+    if (v < 1) return false;
+    if (k == "alloc") *kind = (int)Fault::Alloc;
+    else if (k == "launch") *kind = (int)Fault::Launch;
+    else if (k == "timeout") *kind = (int)Fault::Timeout;
+    else return false;
+    *n = v;
+    return true;
+}
+
+static void fault_from_env() {
+    std::call_once(g_fault_env, [] {
+        int kind;
+        long long n;
+        if (parse_fault(std::getenv("RR_FAULT"), &kind, &n) && kind) {
+            g_fault_left.store(n);
+            g_fault_kind.store(kind);
+        }
+    });
+}
+
+bool fault_fires(Fault kind) {
+    fault_from_env();
+    if (g_fault_kind.load(std::memory_order_relaxed) != (int)kind) return false;
+    if (g_fault_left.fetch_sub(1) != 1) return false;
+    g_fault_kind.store(0);
+    return true;
+}
+
+cudaError_t lib_malloc(void **p, size_t bytes) {
+    if (fault_fires(Fault::Alloc)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t s) {
+    if (fault_fires(Fault::Alloc)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, s);
 }
 
 DeviceState *device_state(rr_status *st) {
@@ -58,7 +121,7 @@ DeviceState *device_state(rr_status *st) {
         // the error words and the trace queue counters live in one allocation
         const size_t words = kErrorWords + 2 * (size_t)(kQueueSlots + kCaptureQueueSlots);
         uint32_t *mem = nullptr;
-        e = cudaMalloc(&mem, sizeof(uint32_t) * words);
+        e = lib_malloc(reinterpret_cast<void **>(&mem), sizeof(uint32_t) * words);
         if (e != cudaSuccess) {
             *st = fail_cuda(e, "device state allocation");
             return nullptr;
@@ -240,5 +303,16 @@ extern "C" const char *rr_status_string(rr_status s) {
 }
 
 extern "C" const char *rr_last_error_message(void) { return t_last_error.c_str(); }
+
+extern "C" rr_status rr_fault_inject(const char *spec) {
+    int kind;
+    long long n;
+    fault_from_env();  // the environment's spec, if any, is replaced below
+    if (!parse_fault(spec, &kind, &n)) return fail(RR_ERR_INVALID_ARG, "rr_fault_inject: bad spec");
+    g_fault_kind.store(0);
+    g_fault_left.store(n);
+    g_fault_kind.store(kind);
+    return RR_OK;
+}
 
 extern "C" uint64_t rr_kernel_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }

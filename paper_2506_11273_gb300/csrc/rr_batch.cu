@@ -197,7 +197,7 @@ extern "C" rr_status rr_batch_create(const rr_wavefront *fronts, uint32_t n_fron
     off = up(off + 4ull * nsort);
     const size_t o_ws = off;
     off = up(off + b->sort_ws_bytes);
-    cudaError_t e = cudaMalloc(&b->mem, off);
+    cudaError_t e = lib_malloc(reinterpret_cast<void **>(&b->mem), off);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete b;
@@ -216,6 +216,7 @@ extern "C" rr_status rr_batch_create(const rr_wavefront *fronts, uint32_t n_fron
         segs[k].tris = reinterpret_cast<const float4 *>(h->tris);
         segs[k].planes = h->planes;
         segs[k].n_nodes = h->n_nodes;
+        segs[k].n_tris = h->n_tris;
         segs[k].table = accumulating(b) ? fronts[k].table->cells : nullptr;
         segs[k].invE = 0.0f;
         std::memset(&segs[k].frame, 0, sizeof(QuantFrame));
@@ -363,7 +364,7 @@ extern "C" rr_status rr_batch_tune(rr_batch *b, const float *o_tmin, const float
     const size_t tbytes = sizeof(unsigned long long) * 2 * kTableCells;
     for (unsigned long long *t : b->tables) {
         unsigned long long *c = nullptr;
-        if (cudaMalloc(&c, tbytes) != cudaSuccess) {
+        if (lib_malloc(reinterpret_cast<void **>(&c), tbytes) != cudaSuccess) {
             cudaGetLastError();
             for (unsigned long long *x : saved) cudaFree(x);
             return fail(RR_ERR_OOM, "rr_batch_tune: no room to save the length tables");

@@ -15,6 +15,7 @@ struct BatchScene {
     const float4 *tris;
     const float4 *planes;
     uint32_t n_nodes;
+    uint32_t n_tris;
     unsigned long long *table;  // cells {sum, count}; null: no adaptive estimate, no update
     QuantFrame frame;           // make_frame of the wavefront's box (computed on the device)
     float invE;                 // 1 / frame.E

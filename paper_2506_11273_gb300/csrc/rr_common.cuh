@@ -81,11 +81,38 @@ void *mapped_host_range(const void *host, size_t bytes);
 // may be using for its own work.  Enqueued on `s`.
 rr_status enqueue_kernel_copy(void *dst, const void *src, size_t bytes, int sm_count, cudaStream_t s);
 
+// Host-side fault injection (rr_fault_inject, or RR_FAULT in the environment):
+// returns true exactly once, at the N-th call of that kind after the spec was
+// set.  Kinds: library device allocations, launch checks, bounded host waits.
+enum class Fault { Alloc = 1, Launch = 2, Timeout = 3 };
+bool fault_fires(Fault kind);
+
+// Library-owned device allocations (an injected Alloc fault fails them).
+cudaError_t lib_malloc(void **p, size_t bytes);
+cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t s);
+
 // Counts kernel launches made by the library.
 void note_launches(uint32_t k);
 
 // A kernel launch check: returns RR_OK or RR_ERR_CUDA with the message recorded.
 rr_status check_launch(const char *what);
+
+// Index checks of the bounds-checked build (compiled with RR_CHECKED, library
+// librr_checked.so): an index outside its buffer records RR_DEVERR_BAD_INDEX
+// in the error word and the access is skipped.  Compiled out otherwise.
+#ifdef RR_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+#ifdef __CUDACC__
+__device__ __forceinline__ bool index_ok(uint32_t i, uint32_t n, uint32_t *err) {
+    if (!kChecked || i < n) return true;
+    atomicOr(err, RR_DEVERR_BAD_INDEX);
+    return false;
+}
+#endif
 
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 inline bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }

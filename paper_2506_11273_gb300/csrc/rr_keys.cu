@@ -399,7 +399,7 @@ extern "C" rr_status rr_length_table_create(const float lo[3], const float hi[3]
         delete t;
         return fail(RR_ERR_INVALID_ARG, "rr_length_table_create: box has zero extent");
     }
-    cudaError_t e = cudaMalloc(&t->cells, sizeof(unsigned long long) * 2 * kTableCells);
+    cudaError_t e = lib_malloc(reinterpret_cast<void **>(&t->cells), sizeof(unsigned long long) * 2 * kTableCells);
     if (e != cudaSuccess) {
         delete t;
         cudaGetLastError();

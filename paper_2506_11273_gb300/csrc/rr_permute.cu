@@ -15,7 +15,7 @@ __global__ void __launch_bounds__(kPermuteBlock) permute_kernel(const float4 *__
                                                                const uint32_t *__restrict__ perm, uint32_t n,
                                                                float4 *__restrict__ o_out,
                                                                float4 *__restrict__ d_out,
-                                                               uint32_t *__restrict__ p_out) {
+                                                               uint32_t *__restrict__ p_out, uint32_t *err) {
     const uint32_t base = blockIdx.x * (kPermuteBlock * kPermuteItems) + threadIdx.x;
     uint32_t src[kPermuteItems];
 #pragma unroll
@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(kPermuteBlock) permute_kernel(const float4 *__
 #pragma unroll
     for (int j = 0; j < kPermuteItems; ++j) {
         const uint32_t i = base + j * kPermuteBlock;
-        if (i < n) {
+        if (i < n && index_ok(src[j], n, err)) {
             o[j] = __ldg(o_in + src[j]);
             d[j] = __ldg(d_in + src[j]);
             if (PAYLOAD) p[j] = __ldg(p_in + src[j]);
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kPermuteBlock) permute_kernel(const float4 *__
 #pragma unroll
     for (int j = 0; j < kPermuteItems; ++j) {
         const uint32_t i = base + j * kPermuteBlock;
-        if (i < n) {
+        if (i < n && (!kChecked || src[j] < n)) {
             o_out[i] = o[j];
             d_out[i] = d[j];
             if (PAYLOAD) p_out[i] = p[j];
@@ -68,7 +68,8 @@ extern "C" rr_status rr_permute(const float *o_tmin_in, const float *d_tmax_in, 
         (payload_in && (overlaps(payload_out, pb, payload_in, pb) || overlaps(payload_out, pb, perm, pb))))
         return fail(RR_ERR_INVALID_ARG, "rr_permute: buffers overlap");
     rr_status st;
-    if (!device_state(&st)) return st;
+    DeviceState *ds = device_state(&st);
+    if (!ds) return st;
     const uint32_t per_block = kPermuteBlock * kPermuteItems;
     dim3 grid((n + per_block - 1) / per_block);
     cudaStream_t s = as_stream(stream);
@@ -76,10 +77,11 @@ extern "C" rr_status rr_permute(const float *o_tmin_in, const float *d_tmax_in, 
     const float4 *di = reinterpret_cast<const float4 *>(d_tmax_in);
     float4 *oo = reinterpret_cast<float4 *>(o_tmin_out);
     float4 *dd = reinterpret_cast<float4 *>(d_tmax_out);
+    uint32_t *err = error_word(ds, s);
     if (payload_in)
-        permute_kernel<true><<<grid, kPermuteBlock, 0, s>>>(oi, di, payload_in, perm, n, oo, dd, payload_out);
+        permute_kernel<true><<<grid, kPermuteBlock, 0, s>>>(oi, di, payload_in, perm, n, oo, dd, payload_out, err);
     else
-        permute_kernel<false><<<grid, kPermuteBlock, 0, s>>>(oi, di, nullptr, perm, n, oo, dd, nullptr);
+        permute_kernel<false><<<grid, kPermuteBlock, 0, s>>>(oi, di, nullptr, perm, n, oo, dd, nullptr, err);
     note_launches(1);
     return check_launch("rr_permute");
 }

@@ -83,7 +83,7 @@ extern "C" rr_status rr_pipeline_create(const rr_bvh *bvh, uint32_t max_n, const
         sl[4] = take(16ull * max_n);  // hits
     }
     rr_pipeline *p = new rr_pipeline();
-    cudaError_t e = cudaMalloc(&p->mem, off);
+    cudaError_t e = lib_malloc(reinterpret_cast<void **>(&p->mem), off);
     if (e != cudaSuccess) {
         delete p;
         cudaGetLastError();
@@ -248,6 +248,7 @@ extern "C" rr_status rr_pipeline_wait(rr_pipeline *p, uint64_t ticket) {
     if (!p) return fail(RR_ERR_INVALID_ARG, "rr_pipeline_wait: NULL pipeline");
     if (ticket == 0) return RR_OK;  // an empty submission
     if (ticket > p->submitted) return fail(RR_ERR_INVALID_ARG, "rr_pipeline_wait: ticket was never issued");
+    if (fault_fires(Fault::Timeout)) return fail(RR_ERR_TIMEOUT, "rr_pipeline_wait: injected time-out");
     // a slot's events are re-recorded by later submissions; those complete
     // after this one, so waiting on them is never too early.  `done` follows
     // every earlier submission on the caller's stream and `pay_down` every

@@ -160,7 +160,8 @@ rr_status launch_group(rr_server *s, Group *g) {
     rr_sort_workspace_size((uint32_t)std::max<uint64_t>(n, 1), total_bits, s->cfg.radix_bits, &ws);
     unsigned char *mem = nullptr;
     cudaError_t e = cudaEventRecord(sl.ev[0], st);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&mem), g->bytes, st);
+    if (e == cudaSuccess) e = lib_malloc_async(reinterpret_cast<void **>(&mem), g->bytes, st);
+    if (e == cudaErrorMemoryAllocation) return fail(RR_ERR_OOM, "rr_server: group memory could not be allocated");
     if (e != cudaSuccess) return fail_cuda(e, "rr_server: cudaMallocAsync");
     size_t off = 0;
     float *o = reinterpret_cast<float *>(mem + off);
@@ -381,7 +382,7 @@ extern "C" rr_status rr_server_create(const rr_server_config *cfg, rr_server **o
         if (e == cudaSuccess) *sl.h_err = 0u;
         for (cudaEvent_t &ev : sl.ev)
             if (e == cudaSuccess) e = cudaEventCreate(&ev);
-        if (e == cudaSuccess) e = cudaMalloc(&sl.queue, 2 * sizeof(uint32_t));
+        if (e == cudaSuccess) e = lib_malloc(reinterpret_cast<void **>(&sl.queue), 2 * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMemset(sl.queue, 0, 2 * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&sl.h_segs), sizeof(BatchScene) * kMaxBatchSegments);
         if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&sl.h_offs), 4ull * (kMaxBatchSegments + 1));
@@ -437,12 +438,13 @@ extern "C" rr_status rr_server_add_scene(rr_server *s, const rr_bvh *bvh, rr_len
     h.tris = reinterpret_cast<const float4 *>(bvh->tris);
     h.planes = bvh->planes;
     h.n_nodes = bvh->n_nodes;
+    h.n_tris = bvh->n_tris;
     h.table = adaptive(s) ? table->cells : nullptr;
     float box[6] = {aabb_lo[0], aabb_lo[1], aabb_lo[2], aabb_hi[0], aabb_hi[1], aabb_hi[2]};
     BatchScene *dseg = nullptr;
     float *dbox = nullptr;
-    cudaError_t e = cudaMalloc(&dseg, sizeof(BatchScene));
-    if (e == cudaSuccess) e = cudaMalloc(&dbox, sizeof(box));
+    cudaError_t e = lib_malloc(reinterpret_cast<void **>(&dseg), sizeof(BatchScene));
+    if (e == cudaSuccess) e = lib_malloc(reinterpret_cast<void **>(&dbox), sizeof(box));
     if (e == cudaSuccess) e = cudaMemcpy(dseg, &h, sizeof(BatchScene), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dbox, box, sizeof(box), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = launch_batch_frames(dseg, dbox, 1, nullptr);
@@ -501,6 +503,7 @@ extern "C" rr_status rr_server_wait(rr_server *s, uint64_t ticket, double timeou
     auto it = s->all.find(ticket);
     if (it == s->all.end()) return fail(RR_ERR_INVALID_ARG, "rr_server_wait: unknown or released ticket");
     Request *r = it->second;
+    if (fault_fires(Fault::Timeout)) return fail(RR_ERR_TIMEOUT, "rr_server_wait: injected time-out");
     const auto until = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
     while (!r->done) {
         if (s->cv.wait_until(lock, until) == std::cv_status::timeout && !r->done)

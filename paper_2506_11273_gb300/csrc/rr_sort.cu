@@ -320,6 +320,7 @@ __device__ __forceinline__ void onesweep_tile(const PassArgs<K> &a, uint32_t til
             const uint32_t i = j * kSortBlock + tid;
             const K key = s_keys[i];
             const uint32_t gpos = s_gbase[digit_of(key, a.shift, a.mask)] + i;
+            if (!index_ok(gpos, a.n, a.err)) continue;
             if (a.keys_out) a.keys_out[gpos] = key;
             a.vals_out[gpos] = s_vals[i];
         }
@@ -328,6 +329,7 @@ __device__ __forceinline__ void onesweep_tile(const PassArgs<K> &a, uint32_t til
         for (uint32_t i = tid; i < tile_n; i += kSortBlock) {
             const K key = s_keys[i];
             const uint32_t gpos = s_gbase[digit_of(key, a.shift, a.mask)] + i;
+            if (!index_ok(gpos, a.n, a.err)) continue;
             if (a.keys_out) a.keys_out[gpos] = key;
             a.vals_out[gpos] = s_vals[i];
         }
@@ -603,6 +605,7 @@ static rr_status run_sort(const SortPlan &pl, const K *keys_in, K *keys_out, uin
     const cudaError_t e = enqueue_sort<K, RBITS>(pl, keys_in, keys_out, perm_out, n, bits, ws, err, nullptr,
                                                  sm_count, s);
     if (e != cudaSuccess) return fail_cuda(e, "rr_sort");
+    if (fault_fires(Fault::Launch)) return fail(RR_ERR_CUDA, "rr_sort: injected launch failure");
     return RR_OK;
 }
 

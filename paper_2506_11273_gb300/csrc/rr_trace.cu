@@ -32,6 +32,7 @@ struct SceneRef {
     const float4 *tris;    // RRTri as three float4
     const float4 *planes;  // two float4 per triangle: normal hi.xyz, lo.x | lo.y, lo.z
     uint32_t n_nodes;
+    uint32_t n_tris;
 };
 
 struct TraceArgs {
@@ -154,12 +155,19 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
 // Node part of a traversal round: visit the nearest node of the current group
 // (its hit inner children become the current group, its hit leaves the
 // pending triangle group).
-__device__ __forceinline__ bool ray_visit_node(RayState &r, uint2 *stack, const SceneRef &a) {
+__device__ __forceinline__ bool ray_visit_node(RayState &r, uint2 *stack, const SceneRef &a, uint32_t *err) {
     const float tmin = r.o.w;
     const uint32_t pos = __ffs(r.g_hits) - 1u;
     r.g_hits &= r.g_hits - 1u;
     const uint32_t slot = pos ^ r.negmask;
     const uint32_t node = r.g_base + __popc(r.g_imask & ((1u << slot) - 1u));
+    if (!index_ok(node, a.n_nodes, err)) {  // checked build: end the ray as a miss
+        r.best_tri = kMiss;
+        r.g_hits = 0u;
+        r.t_hits = 0u;
+        r.sp = 0;
+        return true;
+    }
     if (r.g_hits != 0u) {
         if (r.sp >= (int)kTraceStack) return false;
         stack[r.sp++] = make_uint2(r.g_base, r.g_hits | (r.g_imask << 8));
@@ -239,11 +247,12 @@ __device__ __forceinline__ bool ray_visit_node(RayState &r, uint2 *stack, const 
 // traversal step).  ANY: a hit ends the ray (the pending group, the current
 // node group and the stack are dropped).
 template <bool ANY>
-__device__ __forceinline__ void test_one_triangle(RayState &r, const SceneRef &a) {
+__device__ __forceinline__ void test_one_triangle(RayState &r, const SceneRef &a, uint32_t *err) {
     const float tmin = r.o.w;
     const uint32_t b = __ffs(r.t_hits) - 1u;
     r.t_hits &= r.t_hits - 1u;
     const uint32_t k = r.t_base + __popc(r.t_all & ((1u << b) - 1u));
+    if (!index_ok(k, a.n_tris, err)) return;
     const float4 *tp = a.tris + 3 * (size_t)k;
     const float4 v0 = __ldg(tp), e1 = __ldg(tp + 1), e2 = __ldg(tp + 2);
     const float4 d = r.d, o = r.o;
@@ -306,7 +315,7 @@ __device__ __forceinline__ void accumulate_hit(unsigned long long *table, const 
 template <bool ANY>
 __device__ __forceinline__ bool ray_step(RayState &r, uint2 *stack, const SceneRef &sc, uint32_t *err) {
     if (r.t_hits != 0u) {
-        test_one_triangle<ANY>(r, sc);
+        test_one_triangle<ANY>(r, sc, err);
         return true;
     }
     if (r.g_hits == 0u) {
@@ -316,7 +325,7 @@ __device__ __forceinline__ bool ray_step(RayState &r, uint2 *stack, const SceneR
         r.g_hits = e.y & 0xFFu;
         r.g_imask = (e.y >> 8) & 0xFFu;
     }
-    if (!ray_visit_node(r, stack, sc)) {
+    if (!ray_visit_node(r, stack, sc, err)) {
         atomicOr(err, RR_DEVERR_TRACE_STACK);
         r.best_tri = kMiss;
         r.g_hits = 0u;
@@ -376,6 +385,7 @@ __global__ void __launch_bounds__(BLOCK, (trace_min_blocks<BLOCK>())) trace_kern
             s_sc[k].tris = bs->tris;
             s_sc[k].planes = bs->planes;
             s_sc[k].n_nodes = bs->n_nodes;
+            s_sc[k].n_tris = bs->n_tris;
         }
     }
     if (MULTI || ACCUM) __syncthreads();
@@ -482,9 +492,9 @@ extern "C" rr_status rr_build_bvh(const float *tris_host, uint32_t n_tris, rr_bv
     b->root_leaf_ref = 0;
     cudaError_t e = cudaSuccess;
     if (b->n_nodes) {
-        e = cudaMalloc(&b->nodes, sizeof(RRNode8) * h.nodes.size());
-        if (e == cudaSuccess) e = cudaMalloc(&b->tris, sizeof(RRTri) * h.tris.size());
-        if (e == cudaSuccess) e = cudaMalloc(&b->planes, sizeof(float4) * h.planes.size());
+        e = lib_malloc(reinterpret_cast<void **>(&b->nodes), sizeof(RRNode8) * h.nodes.size());
+        if (e == cudaSuccess) e = lib_malloc(reinterpret_cast<void **>(&b->tris), sizeof(RRTri) * h.tris.size());
+        if (e == cudaSuccess) e = lib_malloc(reinterpret_cast<void **>(&b->planes), sizeof(float4) * h.planes.size());
         if (e == cudaSuccess)
             e = cudaMemcpy(b->planes, h.planes.data(), sizeof(float4) * h.planes.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
@@ -588,6 +598,7 @@ rr_status launch_trace(const rr_bvh *b, const float *o_tmin, const float *d_tmax
     a.scene.tris = reinterpret_cast<const float4 *>(b->tris);
     a.scene.planes = b->planes;
     a.scene.n_nodes = b->n_nodes;
+    a.scene.n_tris = b->n_tris;
     a.o_tmin = reinterpret_cast<const float4 *>(o_tmin);
     a.d_tmax = reinterpret_cast<const float4 *>(d_tmax);
     a.hits = reinterpret_cast<float4 *>(hits_out);

@@ -21,7 +21,9 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "librr.so")
+# RR_LIBRARY=checked selects the bounds-checked build (librr_checked.so), where
+# every kernel index is checked against its buffer (RR_DEVERR_BAD_INDEX).
+LIB_PATH = os.path.join(_HERE, "librr_checked.so" if os.environ.get("RR_LIBRARY") == "checked" else "librr.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -54,7 +56,7 @@ EXPORTS = [
     "rr_coherence_capsule", "rr_trace_ex", "rr_sort_segments", "rr_batch_create", "rr_batch_destroy",
     "rr_batch_info", "rr_batch_run", "rr_batch_run_loop", "rr_batch_tune", "rr_server_create",
     "rr_server_add_scene", "rr_server_submit", "rr_server_wait", "rr_server_stats", "rr_server_destroy",
-    "rr_selftest_lookback_timeout", "rr_stream_error", "rr_bvh_aabb",
+    "rr_selftest_lookback_timeout", "rr_stream_error", "rr_bvh_aabb", "rr_fault_inject",
 ]
 
 
@@ -161,6 +163,7 @@ def lib():
             L.rr_coherence_capsule.argtypes = [vp, vp, vp, u32, u32, C.c_float, vp, vp]
             L.rr_device_error.argtypes = [C.POINTER(C.c_uint32)]
             L.rr_stream_error.argtypes = [vp, vp]
+            L.rr_fault_inject.argtypes = [C.c_char_p]
             L.rr_bvh_aabb.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
             L.rr_status_string.argtypes = [i32]
             L.rr_status_string.restype = C.c_char_p
@@ -611,6 +614,12 @@ def rr_stream_error(flags_out, stream=None):
     if flags_out.dtype != torch.int32 or flags_out.numel() < 1:
         raise ValueError("flags_out must hold one int32")
     _check(lib().rr_stream_error(_stream(stream), flags_out.data_ptr()), "rr_stream_error")
+
+
+def rr_fault_inject(spec: str | None):
+    """Host-side fault injection: "alloc@N", "launch@N", "timeout@N", or None
+    to clear (see include/rr.h)."""
+    _check(lib().rr_fault_inject(spec.encode() if spec else None), "rr_fault_inject")
 
 
 def rr_bvh_aabb(bvh: "BVH"):
