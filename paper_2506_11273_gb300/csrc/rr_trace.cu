@@ -24,7 +24,7 @@
 
 namespace rr {
 
-constexpr int kTraceBlock = 256;
+constexpr int kTraceBlock = 128;
 
 // The BVH arrays of one scene.
 struct SceneRef {
@@ -340,11 +340,12 @@ __device__ __forceinline__ bool ray_step(RayState &r, uint2 *stack, const SceneR
 // lanes take consecutive queue positions together.
 constexpr uint32_t kRefillLanes = 8;
 
-// Resident blocks asked of the compiler: 32 warps per SM (64 registers: the
-// step loop keeps the ray's state and the refill bookkeeping without spills).
+// Resident blocks asked of the compiler: 36 warps per SM (nine 128-thread
+// blocks at 56 registers; the step loop keeps the ray's state and the refill
+// bookkeeping without spills).  Larger blocks round down to 32 warps.
 template <int BLOCK>
 constexpr int trace_min_blocks() {
-    return 1024 / BLOCK > 0 ? 1024 / BLOCK : 1;
+    return 1152 / BLOCK > 0 ? 1152 / BLOCK : 1;
 }
 
 // Dynamic shared memory of the batch kernels: the scene of every segment, then
