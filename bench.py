@@ -242,19 +242,26 @@ def run_ours(args):
 
     def make_step(B, params, accumulate, bits=KEY_BITS, sort="global", segment=2048, reorder="gather"):
         """One bounce: key -> sort (global onesweep, or local per segment) ->
-        reorder (gather the SoA, or trace through the permutation) -> trace."""
+        reorder (gather the SoA, or trace through the permutation) -> trace.
+        sort="fused": keys and global sort in one rr_key_sort call (the sort's
+        digit counting done by the key kernel); its time is the key phase and
+        the sort phase reads zero."""
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
         keys, ws = (B["keys"], B["ws"]) if bits > 32 else (B["keys32"], B["ws32"])
         tbl = table if accumulate else None
 
         def step():
             ev[0].record(stream)
-            rr.rr_compute_keys(B["o"], B["d"], params, keys)
-            ev[1].record(stream)
-            if sort == "global":
-                rr.rr_sort(keys, None, B["perm"], B["n"], bits, RADIX_BITS, ws)
+            if sort == "fused":
+                rr.rr_key_sort(B["o"], B["d"], params, keys, B["perm"], RADIX_BITS, ws)
+                ev[1].record(stream)
             else:
-                rr.rr_sort_segments(keys, None, B["perm"], B["n"], bits, segment)
+                rr.rr_compute_keys(B["o"], B["d"], params, keys)
+                ev[1].record(stream)
+                if sort == "global":
+                    rr.rr_sort(keys, None, B["perm"], B["n"], bits, RADIX_BITS, ws)
+                else:
+                    rr.rr_sort_segments(keys, None, B["perm"], B["n"], bits, segment)
             ev[2].record(stream)
             if reorder == "gather":
                 rr.rr_permute(B["o"], B["d"], B["p"], B["perm"], B["so"], B["sd"], B["sp"])
@@ -307,12 +314,16 @@ def run_ours(args):
     head = fronts[args.bounce - 1]
     B = bounce_buffers(head)
     n = B["n"]
-    step_tp, phases_tp = make_step(B, params_tp, True)
+    step_tp, phases_tp = make_step(B, params_tp, True, sort="fused")
     l0 = rr.rr_kernel_launch_count()
     with ClockSampler(local) as clk:
         total_ms, times, ph = timed(step_tp, args.steps, args.warmup, phases_tp)
     launches = (rr.rr_kernel_launch_count() - l0)
     launches_timed = launches * args.steps // (args.steps + args.warmup)
+    # the same step with keys and sort as two calls: the key and sort phases
+    # on their own (for their HBM fractions)
+    step_sep, phases_sep = make_step(B, params_tp, True)
+    _, _, ph_sep = timed(step_sep, max(3, args.steps // 2), 3, phases_sep)
     E_scene = float(np.max(hi - lo))
 
     def capsule_mean(o_, d_, h_):
@@ -325,8 +336,10 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     value = whole_job_mrays(world, n, args.steps, total_ms)
     ph = np.array(ph)
-    phase_ms = dict(zip(["key", "sort", "gather", "trace_and_accum", "spare"], [float(x) for x in np.median(ph, axis=0)]))
-    phase_ms.pop("spare")
+    med_f = [float(x) for x in np.median(ph, axis=0)]
+    med_s = [float(x) for x in np.median(np.array(ph_sep), axis=0)]
+    phase_ms = {"key_and_sort": med_f[0], "gather": med_f[2], "trace_and_accum": med_f[3],
+                "key": med_s[0], "sort": med_s[1]}
     if rr.rr_device_error() != 0:
         raise RuntimeError("device error flag set during the bench")
 
@@ -423,7 +436,7 @@ def run_ours(args):
         per_bounce = []
         for b, fr in enumerate(fronts, start=1):
             Bb = bounce_buffers(fr)
-            st, pf = make_step(Bb, params_tp, False)
+            st, pf = make_step(Bb, params_tp, False, sort="fused")
             k = 5
             tot_s, _, phb = timed(st, k, 3, pf)
             tot_uu, _, _ = timed(make_unsorted(Bb), k, 3)
@@ -492,6 +505,10 @@ def run_ours(args):
     sort_ach = BYTES_SORT * n / (phase_ms["sort"] * 1e-3) / 1e9
     gather_ach = BYTES_GATHER * n / (phase_ms["gather"] * 1e-3) / 1e9
     key_ach = BYTES_KEY * n / (phase_ms["key"] * 1e-3) / 1e9
+    # fused: the key kernel's reads and writes plus the digit passes (the
+    # counting pass's read of the keys is gone)
+    bytes_key_sort = BYTES_KEY + BYTES_SORT - 8
+    key_sort_ach = bytes_key_sort * n / (phase_ms["key_and_sort"] * 1e-3) / 1e9
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
@@ -503,6 +520,7 @@ def run_ours(args):
                    else "small profiling case",
                    "rays_per_step": n, "triangles": int(info.n_tris), "bounce": args.bounce,
                    "key": "two_point_adaptive", "key_bits": KEY_BITS, "radix_bits": RADIX_BITS,
+                   "key_and_sort": "rr_key_sort (the sort's digit counting in the key kernel)",
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 gpu"},
         "unsorted_mrays": round(unsorted, 2),
         "speedup_vs_unsorted": round(value / unsorted, 3),
@@ -513,6 +531,8 @@ def run_ours(args):
             "sort": {"gbs": round(sort_ach, 1), "frac": round(sort_ach / hbm, 3), "bytes_per_ray": BYTES_SORT,
                      "mkeys_s": round(n / (phase_ms["sort"] * 1e-3) / 1e6, 1)},
             "gather": {"gbs": round(gather_ach, 1), "frac": round(gather_ach / hbm, 3), "bytes_per_ray": BYTES_GATHER},
+            "key_and_sort": {"gbs": round(key_sort_ach, 1), "frac": round(key_sort_ach / hbm, 3),
+                             "bytes_per_ray": bytes_key_sort},
         },
         "e2e": {"value": round(e2e, 2), "unit": UNIT, "h2d_bytes_per_step": 36 * n,
                 "d2h_bytes_per_step": 20 * n,

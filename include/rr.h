@@ -17,6 +17,8 @@
  *
  *   rr_trace_ex          indirect ray access through a permutation (Section 4.4.1)
  *                        and any-hit traversal for shadow rays (Section 4)
+ *   rr_key_sort          keys and their sort in one call, the sort's digit counting
+ *                        fused into the key kernel
  *   rr_sort_segments     local (block-wise) sort (Section 3.2)
  *   rr_coherence_capsule the capsule coherence measure (Section 4.3)
  *   rr_pipeline_*        one bounce behind one handle
@@ -184,6 +186,24 @@ rr_status rr_sort(const void *keys_in, void *keys_out, uint32_t *perm_out, uint3
                   void *stream);
 
 /*
+ * rr_key_sort - the keys of Section 3.1 and their stable radix sort of
+ * Section 3.2 in one call: exactly rr_compute_keys(o_tmin, d_tmax, n, params,
+ * keys_out) followed by rr_sort(keys_out, NULL, perm_out, n, params->bits,
+ * radix_bits, workspace), with the sort's digit counting done by the key
+ * kernel as it produces the keys (the sort's separate counting pass, which
+ * reads every key once more, is not launched).
+ *
+ * keys_out: device, n uint32 (bits <= 32) or n uint64; receives the keys in
+ * input order.  perm_out: device, n uint32; receives the sort permutation.
+ * workspace: as for rr_sort with bits = params->bits.  Every check of
+ * rr_compute_keys and rr_sort applies; the rays must not overlap keys_out,
+ * perm_out or the workspace.  Device errors go to the error word of `stream`.
+ */
+rr_status rr_key_sort(const float *o_tmin, const float *d_tmax, uint32_t n, const rr_key_params *params,
+                      void *keys_out, uint32_t *perm_out, uint32_t radix_bits, void *workspace,
+                      size_t workspace_bytes, void *stream);
+
+/*
  * rr_sort_segments - local (block-wise) sort, Section 3.2: the keys are cut
  * into consecutive segments of `segment` keys (256, 512, 1024, 2048 or 4096;
  * the last segment may be shorter) and each segment is sorted stably by its
@@ -256,6 +276,29 @@ rr_status rr_bvh_destroy(rr_bvh *bvh);
 rr_status rr_bvh_get_info(const rr_bvh *bvh, rr_bvh_info *info);
 /* The scene box: min and max over all vertices (the box the keys quantise in, Section 3). */
 rr_status rr_bvh_aabb(const rr_bvh *bvh, float lo[3], float hi[3]);
+
+/*
+ * rr_bvh_serialize - writes a BVH into host memory, so that a scene's build
+ * (seconds for millions of triangles) can be stored and reloaded.  The format:
+ * a 64-byte header (magic "RRBVH8", format version 1, node size, node and
+ * triangle counts, depth, leaf count, scene box) followed by the node,
+ * triangle and plane arrays as they sit in device memory (little-endian).
+ * buf == NULL: *bytes receives the size needed and nothing is written.
+ * Otherwise *bytes is the capacity of buf (host); a smaller capacity returns
+ * RR_ERR_INVALID_ARG with the size needed in *bytes.  Synchronous.
+ */
+rr_status rr_bvh_serialize(const rr_bvh *bvh, void *buf, size_t *bytes);
+
+/*
+ * rr_bvh_deserialize - a new handle from rr_bvh_serialize's bytes (host),
+ * uploaded to the current device.  The buffer is checked before anything is
+ * uploaded: size against the header, children stored after their parent and
+ * inside the node array, triangles inside the triangle array, leaf bits, depth
+ * within the trace kernel's stack, triangle ids below the count; a buffer that
+ * fails a check returns RR_ERR_INVALID_ARG.  Synchronous; the caller keeps
+ * ownership of buf.
+ */
+rr_status rr_bvh_deserialize(const void *buf, size_t bytes, rr_bvh **out);
 
 /*
  * rr_trace - closest hit of every ray: the smallest t with tmin < t < tmax over
@@ -492,6 +535,26 @@ rr_status rr_batch_run_loop(rr_batch *batch, const float *o_tmin, const float *d
  */
 rr_status rr_batch_tune(rr_batch *batch, const float *o_tmin, const float *d_tmax, float *hits_out,
                         rr_batch_config *best, float *best_ms, void *stream);
+
+/*
+ * rr_batch_tune_cached - rr_batch_tune with its choice kept in a JSON file at
+ * cache_path (host path, created when missing), so that a later process tunes
+ * a batch of the same kind without timing anything.  The entry's key is the
+ * GPU (name, SM count, compute capability), the batch's ray count and
+ * wavefront count each rounded down to a power of two, the wavefront bits, and
+ * the batch's key layout and estimate.  On a hit *best (and *best_ms, the time
+ * recorded with it) come from the file and *from_cache = 1; on a miss, or an
+ * entry this batch cannot run, the batch is tuned, the entry written (the file
+ * is replaced by rename, its other entries kept) and *from_cache = 0.  The file
+ * format: {"format": "rr-batch-tune-cache", "version": 1, "entries":
+ * {"<key>": {"key_bits", "radix_bits", "trace_block", "layout", "ms"}}}; a
+ * malformed file counts as empty and is rewritten.  A file that cannot be
+ * written returns RR_ERR_INVALID_ARG after *best has been filled.
+ * best_ms and from_cache may be NULL.
+ */
+rr_status rr_batch_tune_cached(rr_batch *batch, const float *o_tmin, const float *d_tmax, float *hits_out,
+                               const char *cache_path, rr_batch_config *best, float *best_ms,
+                               uint32_t *from_cache, void *stream);
 
 /* ---------------------------------------------------------------- serving */
 

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "rr_batch.cuh"
+#include "rr_tune_cache.h"
 #include "rr_common.cuh"
 
 using namespace rr;
@@ -442,5 +443,69 @@ extern "C" rr_status rr_batch_tune(rr_batch *b, const float *o_tmin, const float
     if (st != RR_OK) return st;
     *best = win;
     if (best_ms) *best_ms = win_ms;
+    return RR_OK;
+}
+
+namespace {
+
+uint32_t log2_floor(uint32_t x) {
+    uint32_t r = 0;
+    while (x > 1u) {
+        x >>= 1;
+        ++r;
+    }
+    return r;
+}
+
+// The cache key of a batch: what the tuner's choice depends on.  The GPU (name,
+// SM count, compute capability), the batch's size to a power of two, its
+// wavefront count to a power of two, the wavefront bits, and the layout and
+// estimate of its keys.
+std::string tune_key(const rr_batch *b) {
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, b->device);
+    std::string name;
+    for (const char *c = prop.name; *c; ++c)
+        if (*c != '|' && *c != '"' && *c != '\\') name.push_back(*c);
+    return name + "|sm" + std::to_string(prop.multiProcessorCount) + "|cc" + std::to_string(prop.major) + "." +
+           std::to_string(prop.minor) + "|rays2^" + std::to_string(log2_floor(b->n_total)) + "|fronts2^" +
+           std::to_string(log2_floor(b->n_fronts)) + "|seg" + std::to_string(b->seg_bits) + "|layout" +
+           std::to_string((int)b->layout) + "|tsrc" + std::to_string((int)b->tsrc) + "|tuner1";
+}
+
+}  // namespace
+
+extern "C" rr_status rr_batch_tune_cached(rr_batch *b, const float *o_tmin, const float *d_tmax, float *hits_out,
+                                          const char *cache_path, rr_batch_config *best, float *best_ms,
+                                          uint32_t *from_cache, void *stream) {
+    if (!b || !best || !cache_path || !*cache_path)
+        return fail(RR_ERR_INVALID_ARG, "rr_batch_tune_cached: NULL argument");
+    rr_batch_config probe{16, 8, 256, -1};
+    rr_status st = check_run_args(b, o_tmin, d_tmax, hits_out, &probe, "rr_batch_tune_cached");
+    if (st != RR_OK) return st;
+    const std::string key = tune_key(b);
+    TuneEntry e;
+    if (tune_cache_lookup(cache_path, key, &e)) {
+        const rr_batch_config c{e.key_bits, e.radix_bits, e.trace_block, e.layout};
+        // an entry this library could not run (a stale or edited file) is tuned again
+        if (check_run_args(b, o_tmin, d_tmax, hits_out, &c, "rr_batch_tune_cached") == RR_OK) {
+            *best = c;
+            if (best_ms) *best_ms = (float)e.ms;
+            if (from_cache) *from_cache = 1u;
+            return RR_OK;
+        }
+    }
+    float ms = 0.0f;
+    st = rr_batch_tune(b, o_tmin, d_tmax, hits_out, best, &ms, stream);
+    if (st != RR_OK) return st;
+    if (best_ms) *best_ms = ms;
+    if (from_cache) *from_cache = 0u;
+    e.key_bits = best->key_bits;
+    e.radix_bits = best->radix_bits;
+    e.trace_block = best->trace_block;
+    e.layout = best->layout;
+    e.ms = ms;
+    std::string err;
+    if (!tune_cache_store(cache_path, key, e, &err)) return fail(RR_ERR_INVALID_ARG, "rr_batch_tune_cached: " + err);
     return RR_OK;
 }

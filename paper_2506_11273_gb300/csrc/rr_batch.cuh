@@ -1,4 +1,5 @@
-// Internal interface between the batch runtime and the kernels it enqueues.
+// Internal interface between the library's units: the batch runtime, the
+// serving loop and the fused key + sort call, and the kernels they enqueue.
 #pragma once
 
 #include "rr_common.cuh"
@@ -43,5 +44,29 @@ rr_status launch_trace_batch(const BatchScene *segs, const uint32_t *seg_offsets
 // rr_sort with arguments already checked and device errors reported to `err`.
 rr_status sort_enqueue(const void *keys_in, void *keys_out, uint32_t *perm_out, uint32_t n, uint32_t bits,
                        uint32_t radix_bits, void *workspace, uint32_t *err, int sm_count, cudaStream_t s);
+
+// The argument checks of rr_sort, with `what` naming the caller in messages.
+rr_status sort_check(const char *what, const void *keys_in, const void *keys_out, const uint32_t *perm_out,
+                     uint32_t n, uint32_t bits, uint32_t radix_bits, const void *workspace,
+                     size_t workspace_bytes);
+
+// Where a sort's counting stage puts its results inside the workspace: the
+// digit counts [pass][2^radix_bits] (zeroed by the caller, then added to),
+// the tile counters [pass] and the look-back words (zero_count uint4 to
+// clear).  Lets a kernel that produces the keys count their digits itself.
+struct SortCountTarget {
+    uint32_t *hist;
+    uint32_t *counters;
+    uint4 *zero_words;
+    size_t zero_count;
+    uint32_t passes;
+    uint32_t radix_bits;
+};
+SortCountTarget sort_count_target(uint32_t n, uint32_t bits, uint32_t radix_bits, void *workspace);
+
+// The digit passes of rr_sort once the counting stage has filled the
+// workspace (arguments already checked).
+rr_status sort_enqueue_passes(const void *keys_in, void *keys_out, uint32_t *perm_out, uint32_t n, uint32_t bits,
+                              uint32_t radix_bits, void *workspace, uint32_t *err, int sm_count, cudaStream_t s);
 
 }  // namespace rr

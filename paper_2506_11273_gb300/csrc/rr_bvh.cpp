@@ -373,4 +373,121 @@ rr_status build_wide_bvh(const float *tris, uint32_t n, HostBVH *out, std::strin
     return RR_OK;
 }
 
+namespace {
+
+constexpr char kBvhMagic[8] = {'R', 'R', 'B', 'V', 'H', '8', 0, 0};
+constexpr uint32_t kBvhVersion = 1;
+
+struct BvhHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t node_bytes;
+    uint32_t n_nodes;
+    uint32_t n_tris;
+    uint32_t depth;
+    uint32_t n_leaves;
+    float lo[3], hi[3];
+    uint32_t reserved[2];
+};
+static_assert(sizeof(BvhHeader) == kBvhHeaderBytes, "header layout");
+
+}  // namespace
+
+size_t serialized_bvh_bytes(size_t n_nodes, size_t n_tris) {
+    return kBvhHeaderBytes + sizeof(RRNode8) * n_nodes + sizeof(RRTri) * n_tris + 2 * sizeof(float4) * n_tris;
+}
+
+void serialize_bvh(const HostBVH &h, void *out) {
+    BvhHeader hd{};
+    std::memcpy(hd.magic, kBvhMagic, sizeof(kBvhMagic));
+    hd.version = kBvhVersion;
+    hd.node_bytes = (uint32_t)sizeof(RRNode8);
+    hd.n_nodes = (uint32_t)h.nodes.size();
+    hd.n_tris = (uint32_t)h.tris.size();
+    hd.depth = h.depth;
+    hd.n_leaves = h.n_leaves;
+    for (int c = 0; c < 3; ++c) {
+        hd.lo[c] = h.lo[c];
+        hd.hi[c] = h.hi[c];
+    }
+    unsigned char *p = static_cast<unsigned char *>(out);
+    std::memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    std::memcpy(p, h.nodes.data(), sizeof(RRNode8) * h.nodes.size());
+    p += sizeof(RRNode8) * h.nodes.size();
+    std::memcpy(p, h.tris.data(), sizeof(RRTri) * h.tris.size());
+    p += sizeof(RRTri) * h.tris.size();
+    std::memcpy(p, h.planes.data(), sizeof(float4) * h.planes.size());
+}
+
+rr_status deserialize_bvh(const void *buf, size_t bytes, HostBVH *out, std::string *err) {
+    auto refuse = [&](const char *why) {
+        *err = std::string("rr_bvh_deserialize: ") + why;
+        return RR_ERR_INVALID_ARG;
+    };
+    if (!buf || bytes < kBvhHeaderBytes) return refuse("buffer shorter than the header");
+    BvhHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (std::memcmp(hd.magic, kBvhMagic, sizeof(kBvhMagic)) != 0) return refuse("not a serialized BVH");
+    if (hd.version != kBvhVersion) return refuse("unknown format version");
+    if (hd.node_bytes != sizeof(RRNode8)) return refuse("node size differs from this library's");
+    if (hd.n_tris >= (1u << 28)) return refuse("too many triangles");
+    if ((hd.n_tris == 0) != (hd.n_nodes == 0)) return refuse("node and triangle counts disagree");
+    if (bytes != serialized_bvh_bytes(hd.n_nodes, hd.n_tris)) return refuse("size does not match the header");
+    for (int c = 0; c < 3; ++c)
+        if (!std::isfinite(hd.lo[c]) || !std::isfinite(hd.hi[c]) || hd.lo[c] > hd.hi[c]) return refuse("bad box");
+    const unsigned char *p = static_cast<const unsigned char *>(buf) + kBvhHeaderBytes;
+    out->nodes.resize(hd.n_nodes);
+    out->tris.resize(hd.n_tris);
+    out->planes.resize(2 * (size_t)hd.n_tris);
+    std::memcpy(out->nodes.data(), p, sizeof(RRNode8) * hd.n_nodes);
+    p += sizeof(RRNode8) * hd.n_nodes;
+    std::memcpy(out->tris.data(), p, sizeof(RRTri) * hd.n_tris);
+    p += sizeof(RRTri) * hd.n_tris;
+    std::memcpy(out->planes.data(), p, sizeof(float4) * 2 * (size_t)hd.n_tris);
+    // structure: children after their parent (no cycle), indices in range,
+    // leaf bits well formed; the depth is recomputed, not trusted
+    std::vector<uint32_t> depth(hd.n_nodes, 0);
+    if (hd.n_nodes) depth[0] = 1;
+    uint32_t max_depth = hd.n_nodes ? 1u : 0u;
+    for (uint32_t i = 0; i < hd.n_nodes; ++i) {
+        const RRNode8 &nd = out->nodes[i];
+        if (i > 0 && depth[i] == 0) return refuse("a node no parent references");
+        if (nd.imask & ~nd.valid & 0xFFu) return refuse("inner child in an unused slot");
+        if (nd.valid & ~0xFFu) return refuse("slot mask above eight slots");
+        const uint32_t inner = (uint32_t)__builtin_popcount(nd.imask);
+        if (inner) {
+            if (nd.child_base <= i || (uint64_t)nd.child_base + inner > hd.n_nodes)
+                return refuse("child index out of order or out of range");
+            for (uint32_t k = 0; k < inner; ++k) {
+                uint32_t &dc = depth[nd.child_base + k];
+                dc = std::max(dc, depth[i] + 1u);
+                max_depth = std::max(max_depth, dc);
+            }
+        }
+        for (int s = 0; s < 8; ++s) {
+            const uint32_t nib = (nd.tribits >> (4 * s)) & 15u;
+            const bool leaf = ((nd.valid >> s) & 1u) && !((nd.imask >> s) & 1u);
+            if (!leaf && nib != 0u) return refuse("triangle bits in a slot that is not a leaf");
+            if (leaf && nib != 1u && nib != 3u && nib != 7u && nib != 15u) return refuse("leaf triangle bits malformed");
+        }
+        if ((uint64_t)nd.tri_base + (uint32_t)__builtin_popcount(nd.tribits) > hd.n_tris)
+            return refuse("triangle index out of range");
+    }
+    if (max_depth > kTraceStack) return refuse("tree deeper than the trace kernel's stack");
+    for (uint32_t k = 0; k < hd.n_tris; ++k) {
+        uint32_t id;
+        std::memcpy(&id, &out->tris[k].v0_id.w, 4);
+        if (id >= hd.n_tris) return refuse("triangle id out of range");
+    }
+    for (int c = 0; c < 3; ++c) {
+        out->lo[c] = hd.lo[c];
+        out->hi[c] = hd.hi[c];
+    }
+    out->depth = max_depth;
+    out->stack_need = max_depth;
+    out->n_leaves = hd.n_leaves;
+    return RR_OK;
+}
+
 }  // namespace rr

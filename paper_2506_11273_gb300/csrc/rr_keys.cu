@@ -22,6 +22,7 @@ struct KeyArgs {
     const float *t_given;
     const ulonglong2 *table;  // cells {sum, count}
     void *keys;
+    SortCountTarget count;    // the fused form only: where the digit counts go
 };
 
 // The key of one ray (Section 3.1): the first `bits` bits of its layout's
@@ -89,11 +90,21 @@ __device__ __forceinline__ uint64_t ray_key(const QuantFrame &f, float4 o, float
 constexpr int kKeyTile = 256;
 constexpr uint32_t kCopySpinLimit = 1u << 22;  // polls of a copy's barrier before giving up
 
-template <int LAYOUT, int TSRC, typename KeyT>
+// Digit-count entries of the fused form: passes x 2^radix_bits <= 2048 for
+// every key width with 4- or 8-bit digits.
+constexpr int kCountEntries = 2048;
+
+// COUNT (the fused key + sort form): each block also counts the digits of
+// every sort pass of its keys (shared atomics into two copies, even and odd
+// warps), adds its counts to the sort's digit counts once at the end, and
+// clears the sort's look-back words and tile counters, so the separate
+// counting kernel of the sort is not needed.
+template <int LAYOUT, int TSRC, typename KeyT, bool COUNT>
 __global__ void __launch_bounds__(kKeyTile, 6) key_kernel(KeyArgs a) {
     __shared__ __align__(128) float4 s_o[2][kKeyTile];
     __shared__ __align__(128) float4 s_d[2][kKeyTile];
     __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ uint32_t s_cnt[COUNT ? 2 : 1][COUNT ? kCountEntries : 1];
     const uint32_t tid = threadIdx.x;
     const uint32_t tiles = (a.n + kKeyTile - 1) / kKeyTile;
     if (tid == 0) {
@@ -101,8 +112,10 @@ __global__ void __launch_bounds__(kKeyTile, 6) key_kernel(KeyArgs a) {
         mbar_init(&s_bar[1], 1);
         mbar_init_fence();
     }
+    if (COUNT)
+        for (uint32_t i = tid; i < 2u * kCountEntries; i += kKeyTile) (&s_cnt[0][0])[i] = 0u;
     const uint32_t *lut = block_spread6_lut();
-    const QuantFrame f = block_frame(a.lo, a.hi);  // synchronises: barriers and table published
+    const QuantFrame f = block_frame(a.lo, a.hi);  // synchronises: barriers, counters and table published
     auto issue = [&](uint32_t t, uint32_t buf) {
         const uint32_t first = t * kKeyTile;
         const uint32_t bytes = min((uint32_t)kKeyTile, a.n - first) * (uint32_t)sizeof(float4);
@@ -132,10 +145,32 @@ __global__ void __launch_bounds__(kKeyTile, 6) key_kernel(KeyArgs a) {
         const uint32_t i = t * kKeyTile + tid;
         if (i < a.n) {
             const float tg = TSRC == RR_T_GIVEN ? __ldg(a.t_given + i) : 0.0f;
-            static_cast<KeyT *>(a.keys)[i] =
+            const KeyT key =
                 (KeyT)ray_key<LAYOUT, TSRC>(f, s_o[buf][tid], s_d[buf][tid], a.bits, a.ratio, tg, a.table, lut);
+            static_cast<KeyT *>(a.keys)[i] = key;
+            if (COUNT) {
+                // bits above a.bits are zero, so the last pass's digit needs no narrower mask
+                uint32_t *mine = s_cnt[(tid >> 5) & 1u];
+                const uint32_t rb = a.count.radix_bits, mask = (1u << rb) - 1u;
+                KeyT x = key;
+                for (uint32_t p = 0; p < a.count.passes; ++p) {
+                    atomicAdd(&mine[(p << rb) + ((uint32_t)x & mask)], 1u);
+                    x >>= rb;
+                }
+            }
         }
         __syncthreads();  // every thread is done with `buf` before it is refilled
+    }
+    if (COUNT) {
+        __syncthreads();
+        const uint32_t entries = a.count.passes << a.count.radix_bits;
+        for (uint32_t i = tid; i < entries; i += kKeyTile) {
+            const uint32_t c = s_cnt[0][i] + s_cnt[1][i];
+            if (c) atomicAdd(a.count.hist + i, c);
+        }
+        if (blockIdx.x == 0 && tid < a.count.passes) a.count.counters[tid] = 0u;
+        for (size_t w = (size_t)blockIdx.x * kKeyTile + tid; w < a.count.zero_count; w += (size_t)gridDim.x * kKeyTile)
+            a.count.zero_words[w] = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
@@ -178,26 +213,35 @@ __global__ void batch_frame_kernel(BatchScene *segs, const float *boxes, uint32_
 
 // Blocks of one key-kernel variant that fit on the device at once (its
 // occupancy is queried once per variant).
-template <int LAYOUT, int TSRC, typename KeyT>
+template <int LAYOUT, int TSRC, typename KeyT, bool COUNT>
 static uint32_t key_grid(uint32_t tiles, int sm_count) {
     static int bps = 0;
     if (bps == 0) {
         int v = 0;
         const cudaError_t e =
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, key_kernel<LAYOUT, TSRC, KeyT>, kKeyTile, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, key_kernel<LAYOUT, TSRC, KeyT, COUNT>, kKeyTile, 0);
         bps = (e == cudaSuccess && v > 0) ? v : 1;
     }
     return std::max(1u, std::min(tiles, (uint32_t)(sm_count * bps)));
 }
 
-template <int LAYOUT, int TSRC>
-static void launch_keys(const KeyArgs &a, bool wide, int sm_count, cudaStream_t s) {
+template <int LAYOUT, int TSRC, bool COUNT>
+static void launch_keys_t(const KeyArgs &a, bool wide, int sm_count, cudaStream_t s) {
     const uint32_t tiles = (a.n + kKeyTile - 1) / kKeyTile;
     if (wide)
-        key_kernel<LAYOUT, TSRC, unsigned long long>
-            <<<key_grid<LAYOUT, TSRC, unsigned long long>(tiles, sm_count), kKeyTile, 0, s>>>(a);
+        key_kernel<LAYOUT, TSRC, unsigned long long, COUNT>
+            <<<key_grid<LAYOUT, TSRC, unsigned long long, COUNT>(tiles, sm_count), kKeyTile, 0, s>>>(a);
     else
-        key_kernel<LAYOUT, TSRC, uint32_t><<<key_grid<LAYOUT, TSRC, uint32_t>(tiles, sm_count), kKeyTile, 0, s>>>(a);
+        key_kernel<LAYOUT, TSRC, uint32_t, COUNT>
+            <<<key_grid<LAYOUT, TSRC, uint32_t, COUNT>(tiles, sm_count), kKeyTile, 0, s>>>(a);
+}
+
+template <int LAYOUT, int TSRC>
+static void launch_keys(const KeyArgs &a, bool wide, bool count, int sm_count, cudaStream_t s) {
+    if (count)
+        launch_keys_t<LAYOUT, TSRC, true>(a, wide, sm_count, s);
+    else
+        launch_keys_t<LAYOUT, TSRC, false>(a, wide, sm_count, s);
 }
 
 __global__ void table_init_kernel(ulonglong2 *cells) {
@@ -316,69 +360,116 @@ rr_status launch_keys_batch(const BatchScene *segs, const uint32_t *seg_offsets,
 
 using namespace rr;
 
+namespace {
+
+// The checks of rr_compute_keys (and of the key half of rr_key_sort); fills
+// the kernel arguments.  RR_OK with a->n == 0 means nothing to do.
+rr_status key_setup(const char *what, const float *o_tmin, const float *d_tmax, uint32_t n, const rr_key_params *p,
+                    void *keys_out, KeyArgs *a) {
+    const std::string w(what);
+    if (!p) return fail(RR_ERR_INVALID_ARG, w + ": params is NULL");
+    if (p->layout > RR_KEY_OCTAHEDRON) return fail(RR_ERR_INVALID_ARG, w + ": bad layout");
+    if (p->bits < 1 || p->bits > 64) return fail(RR_ERR_INVALID_ARG, w + ": bits not in 1..64");
+    if (p->layout == RR_KEY_TWO_POINT && p->t_source > RR_T_GIVEN)
+        return fail(RR_ERR_INVALID_ARG, w + ": bad t_source");
+    if (!box_ok(p->aabb_lo, p->aabb_hi)) return fail(RR_ERR_INVALID_ARG, w + ": bad box");
+    *a = KeyArgs{};
+    if (n == 0) return RR_OK;
+    if (!o_tmin || !d_tmax || !keys_out) return fail(RR_ERR_INVALID_ARG, w + ": NULL buffer");
+    if (!aligned16(o_tmin) || !aligned16(d_tmax))
+        return fail(RR_ERR_INVALID_ARG, w + ": rays not 16-byte aligned");
+    const bool wide = p->bits > 32;
+    if (!aligned(keys_out, wide ? 8 : 4)) return fail(RR_ERR_INVALID_ARG, w + ": keys misaligned");
+    const size_t kbytes = (wide ? 8ull : 4ull) * n;
+    if (overlaps(keys_out, kbytes, o_tmin, 16ull * n) || overlaps(keys_out, kbytes, d_tmax, 16ull * n))
+        return fail(RR_ERR_INVALID_ARG, w + ": keys overlap the rays");
+    if (p->layout == RR_KEY_TWO_POINT) {
+        if (p->t_source == RR_T_FIXED && !std::isfinite(p->ratio))
+            return fail(RR_ERR_INVALID_ARG, w + ": ratio not finite");
+        if (p->t_source == RR_T_GIVEN && (!p->t_given || !aligned(p->t_given, 4)))
+            return fail(RR_ERR_INVALID_ARG, w + ": t_given missing or misaligned");
+        if (p->t_source == RR_T_ADAPTIVE) {
+            const rr_length_table *t = p->table;
+            if (!t) return fail(RR_ERR_INVALID_ARG, w + ": ADAPTIVE needs a table");
+            if (std::memcmp(t->box.lo, p->aabb_lo, sizeof(float) * 3) ||
+                std::memcmp(t->box.hi, p->aabb_hi, sizeof(float) * 3))
+                return fail(RR_ERR_INVALID_ARG, w + ": table was created for another box");
+            a->table = reinterpret_cast<const ulonglong2 *>(t->cells);
+        }
+    }
+    a->o_tmin = reinterpret_cast<const float4 *>(o_tmin);
+    a->d_tmax = reinterpret_cast<const float4 *>(d_tmax);
+    a->n = n;
+    a->bits = p->bits;
+    for (int c = 0; c < 3; ++c) {
+        a->lo[c] = p->aabb_lo[c];
+        a->hi[c] = p->aabb_hi[c];
+    }
+    a->ratio = p->ratio;
+    a->t_given = p->t_given;
+    a->keys = keys_out;
+    return RR_OK;
+}
+
+// Launches the key kernel of the params' layout and estimate.
+void launch_layout(const rr_key_params *p, const KeyArgs &a, bool count, int sms, cudaStream_t s) {
+    const bool wide = p->bits > 32;
+    switch (p->layout) {
+        case RR_KEY_AILA: launch_keys<RR_KEY_AILA, 0>(a, wide, count, sms, s); break;
+        case RR_KEY_AILA_COMPACT: launch_keys<RR_KEY_AILA_COMPACT, 0>(a, wide, count, sms, s); break;
+        case RR_KEY_ORIGIN: launch_keys<RR_KEY_ORIGIN, 0>(a, wide, count, sms, s); break;
+        case RR_KEY_REIS: launch_keys<RR_KEY_REIS, 0>(a, wide, count, sms, s); break;
+        case RR_KEY_COSTA: launch_keys<RR_KEY_COSTA, 0>(a, wide, count, sms, s); break;
+        case RR_KEY_OCTAHEDRON: launch_keys<RR_KEY_OCTAHEDRON, 0>(a, wide, count, sms, s); break;
+        default:
+            if (p->t_source == RR_T_FIXED)
+                launch_keys<RR_KEY_TWO_POINT, RR_T_FIXED>(a, wide, count, sms, s);
+            else if (p->t_source == RR_T_GIVEN)
+                launch_keys<RR_KEY_TWO_POINT, RR_T_GIVEN>(a, wide, count, sms, s);
+            else
+                launch_keys<RR_KEY_TWO_POINT, RR_T_ADAPTIVE>(a, wide, count, sms, s);
+    }
+}
+
+}  // namespace
+
 extern "C" rr_status rr_compute_keys(const float *o_tmin, const float *d_tmax, uint32_t n,
                                      const rr_key_params *p, void *keys_out, void *stream) {
-    if (!p) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: params is NULL");
-    if (p->layout > RR_KEY_OCTAHEDRON) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: bad layout");
-    if (p->bits < 1 || p->bits > 64) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: bits not in 1..64");
-    if (p->layout == RR_KEY_TWO_POINT && p->t_source > RR_T_GIVEN)
-        return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: bad t_source");
-    if (!box_ok(p->aabb_lo, p->aabb_hi)) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: bad box");
-    if (n == 0) return RR_OK;
-    if (!o_tmin || !d_tmax || !keys_out) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: NULL buffer");
-    if (!aligned16(o_tmin) || !aligned16(d_tmax))
-        return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: rays not 16-byte aligned");
-    const bool wide = p->bits > 32;
-    if (!aligned(keys_out, wide ? 8 : 4)) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: keys misaligned");
     KeyArgs a;
-    a.o_tmin = reinterpret_cast<const float4 *>(o_tmin);
-    a.d_tmax = reinterpret_cast<const float4 *>(d_tmax);
-    a.n = n;
-    a.bits = p->bits;
-    for (int c = 0; c < 3; ++c) {
-        a.lo[c] = p->aabb_lo[c];
-        a.hi[c] = p->aabb_hi[c];
-    }
-    a.ratio = p->ratio;
-    a.t_given = p->t_given;
-    a.table = nullptr;
-    a.keys = keys_out;
-    rr_status st;
+    rr_status st = key_setup("rr_compute_keys", o_tmin, d_tmax, n, p, keys_out, &a);
+    if (st != RR_OK || n == 0) return st;
     DeviceState *ds = device_state(&st);
     if (!ds) return st;
     cudaStream_t s = as_stream(stream);
     a.err = error_word(ds, s);
-    const int sms = ds->sm_count;
-    if (p->layout == RR_KEY_AILA) {
-        launch_keys<RR_KEY_AILA, 0>(a, wide, sms, s);
-    } else if (p->layout == RR_KEY_AILA_COMPACT) {
-        launch_keys<RR_KEY_AILA_COMPACT, 0>(a, wide, sms, s);
-    } else if (p->layout == RR_KEY_ORIGIN) {
-        launch_keys<RR_KEY_ORIGIN, 0>(a, wide, sms, s);
-    } else if (p->layout == RR_KEY_REIS) {
-        launch_keys<RR_KEY_REIS, 0>(a, wide, sms, s);
-    } else if (p->layout == RR_KEY_COSTA) {
-        launch_keys<RR_KEY_COSTA, 0>(a, wide, sms, s);
-    } else if (p->layout == RR_KEY_OCTAHEDRON) {
-        launch_keys<RR_KEY_OCTAHEDRON, 0>(a, wide, sms, s);
-    } else if (p->t_source == RR_T_FIXED) {
-        if (!std::isfinite(p->ratio)) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: ratio not finite");
-        launch_keys<RR_KEY_TWO_POINT, RR_T_FIXED>(a, wide, sms, s);
-    } else if (p->t_source == RR_T_GIVEN) {
-        if (!p->t_given || !aligned(p->t_given, 4))
-            return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: t_given missing or misaligned");
-        launch_keys<RR_KEY_TWO_POINT, RR_T_GIVEN>(a, wide, sms, s);
-    } else {
-        const rr_length_table *t = p->table;
-        if (!t) return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: ADAPTIVE needs a table");
-        if (std::memcmp(t->box.lo, p->aabb_lo, sizeof(float) * 3) ||
-            std::memcmp(t->box.hi, p->aabb_hi, sizeof(float) * 3))
-            return fail(RR_ERR_INVALID_ARG, "rr_compute_keys: table was created for another box");
-        a.table = reinterpret_cast<const ulonglong2 *>(t->cells);
-        launch_keys<RR_KEY_TWO_POINT, RR_T_ADAPTIVE>(a, wide, sms, s);
-    }
+    launch_layout(p, a, false, ds->sm_count, s);
     note_launches(1);
     return check_launch("rr_compute_keys");
+}
+
+extern "C" rr_status rr_key_sort(const float *o_tmin, const float *d_tmax, uint32_t n, const rr_key_params *p,
+                                 void *keys_out, uint32_t *perm_out, uint32_t radix_bits, void *workspace,
+                                 size_t workspace_bytes, void *stream) {
+    KeyArgs a;
+    rr_status st = key_setup("rr_key_sort", o_tmin, d_tmax, n, p, keys_out, &a);
+    if (st != RR_OK) return st;
+    st = sort_check("rr_key_sort", keys_out, nullptr, perm_out, n, p->bits, radix_bits, workspace, workspace_bytes);
+    if (st != RR_OK || n == 0) return st;
+    if (overlaps(perm_out, 4ull * n, o_tmin, 16ull * n) || overlaps(perm_out, 4ull * n, d_tmax, 16ull * n) ||
+        overlaps(workspace, workspace_bytes, o_tmin, 16ull * n) || overlaps(workspace, workspace_bytes, d_tmax, 16ull * n))
+        return fail(RR_ERR_INVALID_ARG, "rr_key_sort: buffers overlap the rays");
+    DeviceState *ds = device_state(&st);
+    if (!ds) return st;
+    cudaStream_t s = as_stream(stream);
+    a.err = error_word(ds, s);
+    a.count = sort_count_target(n, p->bits, radix_bits, workspace);
+    const cudaError_t e = cudaMemsetAsync(a.count.hist, 0, sizeof(uint32_t) * (a.count.passes << radix_bits), s);
+    if (e != cudaSuccess) return fail_cuda(e, "rr_key_sort: memset");
+    launch_layout(p, a, true, ds->sm_count, s);
+    note_launches(1);
+    st = check_launch("rr_key_sort");
+    if (st != RR_OK) return st;
+    return sort_enqueue_passes(keys_out, nullptr, perm_out, n, p->bits, radix_bits, workspace, a.err, ds->sm_count, s);
 }
 
 extern "C" rr_status rr_length_table_create(const float lo[3], const float hi[3], rr_length_table **out,

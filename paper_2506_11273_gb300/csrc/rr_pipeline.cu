@@ -157,9 +157,9 @@ rr_status run_bounce(rr_pipeline *p, const float *o_tmin, const float *d_tmax, c
                      uint32_t n, float *hits_out, uint32_t *payload_out, void *stream, const BounceSync &sync) {
     cudaStream_t s = as_stream(stream);
     rr_status st = wait_on(s, sync.rays_ready);
-    if (st == RR_OK) st = rr_compute_keys(o_tmin, d_tmax, n, &p->params, p->keys, stream);
     if (st == RR_OK)
-        st = rr_sort(p->keys, nullptr, p->perm, n, p->params.bits, p->radix_bits, p->workspace, p->ws_bytes, stream);
+        st = rr_key_sort(o_tmin, d_tmax, n, &p->params, p->keys, p->perm, p->radix_bits, p->workspace, p->ws_bytes,
+                         stream);
     if (st == RR_OK) st = wait_on(s, sync.payload_ready);
     if (st == RR_OK) st = wait_on(s, sync.payload_free);
     if (st == RR_OK)

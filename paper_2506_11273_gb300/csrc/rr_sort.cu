@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "rr_batch.cuh"
 #include "rr_common.cuh"
 
 namespace rr {
@@ -541,20 +542,15 @@ static cudaError_t launch_pass(const PassArgs<K> &a, uint32_t tiles, int sm_coun
     return cudaLaunchKernelEx(&cfg, onesweep_kernel<K, RBITS, 3>, a);
 }
 
-// Enqueues the whole sort: counting pass, one kernel per digit pass.
-// Allocates nothing.  zero_err (may be null) is a device word cleared
-// before the passes run.
+// The counting stage of a sort: the digit counts of every pass start at zero
+// (a memset) and one counting kernel fills them, clearing the look-back words
+// and tile counters.  zero_err (may be null) is a device word cleared too.
 template <typename K, int RBITS>
-static cudaError_t enqueue_sort(const SortPlan &pl, const K *keys_in, K *keys_out, uint32_t *perm_out,
-                                uint32_t n, uint32_t bits, unsigned char *ws, uint32_t *err, uint32_t *zero_err,
-                                int sm_count, cudaStream_t s) {
+static cudaError_t enqueue_count(const SortPlan &pl, const K *keys_in, uint32_t n, uint32_t bits, unsigned char *ws,
+                                 uint32_t *zero_err, int sm_count, cudaStream_t s) {
     uint32_t *hist = reinterpret_cast<uint32_t *>(ws + pl.off_hist);
     uint32_t *counters = reinterpret_cast<uint32_t *>(ws + pl.off_counters);
     unsigned long long *lookback = reinterpret_cast<unsigned long long *>(ws + pl.off_lookback);
-    K *keys_a = reinterpret_cast<K *>(ws + pl.off_keys_a);
-    K *keys_b = reinterpret_cast<K *>(ws + pl.off_keys_b);
-    uint32_t *vals_ws = reinterpret_cast<uint32_t *>(ws + pl.off_vals);
-
     cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * pl.passes * pl.radix, s);
     if (e != cudaSuccess) return e;
     const size_t zero_count = (size_t)pl.passes * pl.tiles * pl.radix / 2;  // uint4 = two words
@@ -567,6 +563,23 @@ static cudaError_t enqueue_sort(const SortPlan &pl, const K *keys_in, K *keys_ou
         1u, std::min({(n + per_block - 1) / per_block, std::max(2u * sms, n / (8u * per_block)), 8u * sms}));
     sort_histogram_kernel<K, RBITS><<<hist_blocks, kSortBlock, 0, s>>>(
         keys_in, n, bits, pl.passes, hist, reinterpret_cast<uint4 *>(lookback), zero_count, counters, zero_err);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+// The digit passes of a sort whose counting stage has run (by enqueue_count
+// or fused into the key kernel): one onesweep kernel per pass.  Allocates
+// nothing.
+template <typename K, int RBITS>
+static cudaError_t enqueue_passes(const SortPlan &pl, const K *keys_in, K *keys_out, uint32_t *perm_out,
+                                  uint32_t n, uint32_t bits, unsigned char *ws, uint32_t *err, int sm_count,
+                                  cudaStream_t s) {
+    uint32_t *hist = reinterpret_cast<uint32_t *>(ws + pl.off_hist);
+    uint32_t *counters = reinterpret_cast<uint32_t *>(ws + pl.off_counters);
+    unsigned long long *lookback = reinterpret_cast<unsigned long long *>(ws + pl.off_lookback);
+    K *keys_a = reinterpret_cast<K *>(ws + pl.off_keys_a);
+    K *keys_b = reinterpret_cast<K *>(ws + pl.off_keys_b);
+    uint32_t *vals_ws = reinterpret_cast<uint32_t *>(ws + pl.off_vals);
     const K *kin = keys_in;
     const uint32_t *vin = nullptr;
     for (uint32_t p = 0; p < pl.passes; ++p) {
@@ -590,13 +603,25 @@ static cudaError_t enqueue_sort(const SortPlan &pl, const K *keys_in, K *keys_ou
         a.lookback = lookback + (size_t)p * pl.tiles * pl.radix;
         a.tile_counter = counters + p;
         a.err = err;
-        e = launch_pass<K, RBITS>(a, pl.tiles, sm_count, s);
+        const cudaError_t e = launch_pass<K, RBITS>(a, pl.tiles, sm_count, s);
         if (e != cudaSuccess) return e;
         kin = kout;
         vin = vout;
     }
-    note_launches(1 + pl.passes);
+    note_launches(pl.passes);
     return cudaGetLastError();
+}
+
+// Enqueues the whole sort: counting stage, one kernel per digit pass.
+// Allocates nothing.  zero_err (may be null) is a device word cleared
+// before the passes run.
+template <typename K, int RBITS>
+static cudaError_t enqueue_sort(const SortPlan &pl, const K *keys_in, K *keys_out, uint32_t *perm_out,
+                                uint32_t n, uint32_t bits, unsigned char *ws, uint32_t *err, uint32_t *zero_err,
+                                int sm_count, cudaStream_t s) {
+    const cudaError_t e = enqueue_count<K, RBITS>(pl, keys_in, n, bits, ws, zero_err, sm_count, s);
+    if (e != cudaSuccess) return e;
+    return enqueue_passes<K, RBITS>(pl, keys_in, keys_out, perm_out, n, bits, ws, err, sm_count, s);
 }
 
 template <typename K, int RBITS>
@@ -628,6 +653,64 @@ rr_status sort_enqueue(const void *keys_in, void *keys_out, uint32_t *perm_out, 
                            : run_sort<unsigned long long, 4>(pl, ki, ko, perm_out, n, bits, ws, err, sm_count, s);
 }
 
+SortCountTarget sort_count_target(uint32_t n, uint32_t bits, uint32_t radix_bits, void *workspace) {
+    const SortPlan pl = plan_sort(n, bits, radix_bits);
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    SortCountTarget t;
+    t.hist = reinterpret_cast<uint32_t *>(ws + pl.off_hist);
+    t.counters = reinterpret_cast<uint32_t *>(ws + pl.off_counters);
+    t.zero_words = reinterpret_cast<uint4 *>(ws + pl.off_lookback);
+    t.zero_count = (size_t)pl.passes * pl.tiles * pl.radix / 2;
+    t.passes = pl.passes;
+    t.radix_bits = radix_bits;
+    return t;
+}
+
+rr_status sort_enqueue_passes(const void *keys_in, void *keys_out, uint32_t *perm_out, uint32_t n, uint32_t bits,
+                              uint32_t radix_bits, void *workspace, uint32_t *err, int sm_count, cudaStream_t s) {
+    const SortPlan pl = plan_sort(n, bits, radix_bits);
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    cudaError_t e;
+    if (pl.kb == 4) {
+        const uint32_t *ki = static_cast<const uint32_t *>(keys_in);
+        uint32_t *ko = static_cast<uint32_t *>(keys_out);
+        e = radix_bits == 8 ? enqueue_passes<uint32_t, 8>(pl, ki, ko, perm_out, n, bits, ws, err, sm_count, s)
+                            : enqueue_passes<uint32_t, 4>(pl, ki, ko, perm_out, n, bits, ws, err, sm_count, s);
+    } else {
+        const unsigned long long *ki = static_cast<const unsigned long long *>(keys_in);
+        unsigned long long *ko = static_cast<unsigned long long *>(keys_out);
+        e = radix_bits == 8
+                ? enqueue_passes<unsigned long long, 8>(pl, ki, ko, perm_out, n, bits, ws, err, sm_count, s)
+                : enqueue_passes<unsigned long long, 4>(pl, ki, ko, perm_out, n, bits, ws, err, sm_count, s);
+    }
+    if (e != cudaSuccess) return fail_cuda(e, "sort passes");
+    if (fault_fires(Fault::Launch)) return fail(RR_ERR_CUDA, "sort passes: injected launch failure");
+    return RR_OK;
+}
+
+rr_status sort_check(const char *what, const void *keys_in, const void *keys_out, const uint32_t *perm_out,
+                     uint32_t n, uint32_t bits, uint32_t radix_bits, const void *workspace,
+                     size_t workspace_bytes) {
+    const std::string w(what);
+    if (bits < 1 || bits > 64) return fail(RR_ERR_INVALID_ARG, w + ": bits not in 1..64");
+    if (radix_bits != 4 && radix_bits != 8) return fail(RR_ERR_INVALID_ARG, w + ": radix_bits must be 4 or 8");
+    if (n >= (1u << 30)) return fail(RR_ERR_INVALID_ARG, w + ": n must be < 2^30");
+    if (n == 0) return RR_OK;
+    if (!keys_in || !perm_out || !workspace) return fail(RR_ERR_INVALID_ARG, w + ": NULL buffer");
+    const SortPlan pl = plan_sort(n, bits, radix_bits);
+    if (workspace_bytes < pl.total) return fail(RR_ERR_INVALID_ARG, w + ": workspace too small");
+    if (!aligned(workspace, 256)) return fail(RR_ERR_INVALID_ARG, w + ": workspace not 256-byte aligned");
+    const size_t kbytes = (size_t)pl.kb * n;
+    if (!aligned(keys_in, pl.kb) || (keys_out && !aligned(keys_out, pl.kb)) || !aligned(perm_out, 4))
+        return fail(RR_ERR_INVALID_ARG, w + ": misaligned buffer");
+    if (overlaps(keys_in, kbytes, perm_out, 4ull * n) ||
+        (keys_out && (overlaps(keys_out, kbytes, keys_in, kbytes) || overlaps(keys_out, kbytes, perm_out, 4ull * n))) ||
+        overlaps(workspace, pl.total, keys_in, kbytes) || overlaps(workspace, pl.total, perm_out, 4ull * n) ||
+        (keys_out && overlaps(workspace, pl.total, keys_out, kbytes)))
+        return fail(RR_ERR_INVALID_ARG, w + ": buffers overlap");
+    return RR_OK;
+}
+
 }  // namespace rr
 
 using namespace rr;
@@ -644,23 +727,8 @@ extern "C" rr_status rr_sort_workspace_size(uint32_t n, uint32_t bits, uint32_t 
 
 extern "C" rr_status rr_sort(const void *keys_in, void *keys_out, uint32_t *perm_out, uint32_t n, uint32_t bits,
                              uint32_t radix_bits, void *workspace, size_t workspace_bytes, void *stream) {
-    if (bits < 1 || bits > 64) return fail(RR_ERR_INVALID_ARG, "rr_sort: bits not in 1..64");
-    if (radix_bits != 4 && radix_bits != 8) return fail(RR_ERR_INVALID_ARG, "rr_sort: radix_bits must be 4 or 8");
-    if (n >= (1u << 30)) return fail(RR_ERR_INVALID_ARG, "rr_sort: n must be < 2^30");
-    if (n == 0) return RR_OK;
-    if (!keys_in || !perm_out || !workspace) return fail(RR_ERR_INVALID_ARG, "rr_sort: NULL buffer");
-    const SortPlan pl = plan_sort(n, bits, radix_bits);
-    if (workspace_bytes < pl.total) return fail(RR_ERR_INVALID_ARG, "rr_sort: workspace too small");
-    if (!aligned(workspace, 256)) return fail(RR_ERR_INVALID_ARG, "rr_sort: workspace not 256-byte aligned");
-    const size_t kbytes = (size_t)pl.kb * n;
-    if (!aligned(keys_in, pl.kb) || (keys_out && !aligned(keys_out, pl.kb)) || !aligned(perm_out, 4))
-        return fail(RR_ERR_INVALID_ARG, "rr_sort: misaligned buffer");
-    if (overlaps(keys_in, kbytes, perm_out, 4ull * n) ||
-        (keys_out && (overlaps(keys_out, kbytes, keys_in, kbytes) || overlaps(keys_out, kbytes, perm_out, 4ull * n))) ||
-        overlaps(workspace, pl.total, keys_in, kbytes) || overlaps(workspace, pl.total, perm_out, 4ull * n) ||
-        (keys_out && overlaps(workspace, pl.total, keys_out, kbytes)))
-        return fail(RR_ERR_INVALID_ARG, "rr_sort: buffers overlap");
-    rr_status st;
+    rr_status st = sort_check("rr_sort", keys_in, keys_out, perm_out, n, bits, radix_bits, workspace, workspace_bytes);
+    if (st != RR_OK || n == 0) return st;
     DeviceState *ds = device_state(&st);
     if (!ds) return st;
     cudaStream_t s = as_stream(stream);

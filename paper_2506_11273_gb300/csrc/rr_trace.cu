@@ -468,20 +468,10 @@ __global__ void __launch_bounds__(BLOCK, (trace_min_blocks<BLOCK>())) trace_kern
 
 using namespace rr;
 
-extern "C" rr_status rr_build_bvh(const float *tris_host, uint32_t n_tris, rr_bvh **out) {
-    if (!out) return fail(RR_ERR_INVALID_ARG, "rr_build_bvh: out is NULL");
-    *out = nullptr;
-    if (n_tris > 0 && !tris_host) return fail(RR_ERR_INVALID_ARG, "rr_build_bvh: tris is NULL");
-    if (n_tris >= (1u << 28)) return fail(RR_ERR_UNSUPPORTED, "rr_build_bvh: at most 2^28 - 1 triangles");
-    rr_status st;
-    if (!device_state(&st)) return st;
-    const auto t0 = std::chrono::steady_clock::now();
-    HostBVH h;
-    std::string err;
-    st = build_wide_bvh(tris_host, n_tris, &h, &err);
-    if (st != RR_OK) return fail(st, err);
-    if (h.stack_need > kTraceStack)
-        return fail(RR_ERR_UNSUPPORTED, "rr_build_bvh: tree needs a deeper traversal stack than the kernel has");
+namespace {
+
+// Uploads a host BVH into a new handle (synchronous).
+rr_status upload_bvh(const HostBVH &h, uint32_t n_tris, double seconds, const char *what, rr_bvh **out) {
     rr_bvh *b = new rr_bvh();
     cudaGetDevice(&b->device);
     b->nodes = nullptr;
@@ -509,7 +499,7 @@ extern "C" rr_status rr_build_bvh(const float *tris_host, uint32_t n_tris, rr_bv
         cudaFree(b->planes);
         delete b;
         cudaGetLastError();
-        return fail(e == cudaErrorMemoryAllocation ? RR_ERR_OOM : RR_ERR_CUDA, "rr_build_bvh: upload failed");
+        return fail(e == cudaErrorMemoryAllocation ? RR_ERR_OOM : RR_ERR_CUDA, std::string(what) + ": upload failed");
     }
     rr_bvh_info &i = b->info;
     i.n_tris = n_tris;
@@ -522,9 +512,76 @@ extern "C" rr_status rr_build_bvh(const float *tris_host, uint32_t n_tris, rr_bv
         i.aabb_lo[c] = h.lo[c];
         i.aabb_hi[c] = h.hi[c];
     }
-    i.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    i.build_seconds = seconds;
     *out = b;
     return RR_OK;
+}
+
+}  // namespace
+
+extern "C" rr_status rr_build_bvh(const float *tris_host, uint32_t n_tris, rr_bvh **out) {
+    if (!out) return fail(RR_ERR_INVALID_ARG, "rr_build_bvh: out is NULL");
+    *out = nullptr;
+    if (n_tris > 0 && !tris_host) return fail(RR_ERR_INVALID_ARG, "rr_build_bvh: tris is NULL");
+    if (n_tris >= (1u << 28)) return fail(RR_ERR_UNSUPPORTED, "rr_build_bvh: at most 2^28 - 1 triangles");
+    rr_status st;
+    if (!device_state(&st)) return st;
+    const auto t0 = std::chrono::steady_clock::now();
+    HostBVH h;
+    std::string err;
+    st = build_wide_bvh(tris_host, n_tris, &h, &err);
+    if (st != RR_OK) return fail(st, err);
+    if (h.stack_need > kTraceStack)
+        return fail(RR_ERR_UNSUPPORTED, "rr_build_bvh: tree needs a deeper traversal stack than the kernel has");
+    return upload_bvh(h, n_tris, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(),
+                      "rr_build_bvh", out);
+}
+
+extern "C" rr_status rr_bvh_serialize(const rr_bvh *b, void *buf, size_t *bytes) {
+    if (!b || !bytes) return fail(RR_ERR_INVALID_ARG, "rr_bvh_serialize: NULL argument");
+    const size_t need = serialized_bvh_bytes(b->n_nodes, b->n_tris);
+    if (!buf) {
+        *bytes = need;
+        return RR_OK;
+    }
+    if (*bytes < need) {
+        *bytes = need;
+        return fail(RR_ERR_INVALID_ARG, "rr_bvh_serialize: buffer too small");
+    }
+    HostBVH h;
+    h.nodes.resize(b->n_nodes);
+    h.tris.resize(b->n_nodes ? b->n_tris : 0);
+    h.planes.resize(2 * h.tris.size());
+    cudaError_t e = cudaSuccess;
+    if (b->n_nodes) {
+        e = cudaMemcpy(h.nodes.data(), b->nodes, sizeof(RRNode8) * h.nodes.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(h.tris.data(), b->tris, sizeof(RRTri) * h.tris.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(h.planes.data(), b->planes, sizeof(float4) * h.planes.size(), cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) return fail_cuda(e, "rr_bvh_serialize: download");
+    for (int c = 0; c < 3; ++c) {
+        h.lo[c] = b->info.aabb_lo[c];
+        h.hi[c] = b->info.aabb_hi[c];
+    }
+    h.depth = b->info.depth;
+    h.n_leaves = b->info.n_leaves;
+    serialize_bvh(h, buf);
+    *bytes = need;
+    return RR_OK;
+}
+
+extern "C" rr_status rr_bvh_deserialize(const void *buf, size_t bytes, rr_bvh **out) {
+    if (!out) return fail(RR_ERR_INVALID_ARG, "rr_bvh_deserialize: out is NULL");
+    *out = nullptr;
+    rr_status st;
+    if (!device_state(&st)) return st;
+    HostBVH h;
+    std::string err;
+    st = deserialize_bvh(buf, bytes, &h, &err);
+    if (st != RR_OK) return fail(st, err);
+    return upload_bvh(h, (uint32_t)h.tris.size(), 0.0, "rr_bvh_deserialize", out);
 }
 
 extern "C" rr_status rr_bvh_destroy(rr_bvh *b) {

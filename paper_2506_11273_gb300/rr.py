@@ -56,7 +56,8 @@ EXPORTS = [
     "rr_coherence_capsule", "rr_trace_ex", "rr_sort_segments", "rr_batch_create", "rr_batch_destroy",
     "rr_batch_info", "rr_batch_run", "rr_batch_run_loop", "rr_batch_tune", "rr_server_create",
     "rr_server_add_scene", "rr_server_submit", "rr_server_wait", "rr_server_stats", "rr_server_destroy",
-    "rr_selftest_lookback_timeout", "rr_stream_error", "rr_bvh_aabb", "rr_fault_inject",
+    "rr_selftest_lookback_timeout", "rr_stream_error", "rr_bvh_aabb", "rr_fault_inject", "rr_key_sort",
+    "rr_bvh_serialize", "rr_bvh_deserialize", "rr_batch_tune_cached",
 ]
 
 
@@ -124,9 +125,12 @@ def lib():
             L.rr_compute_keys.argtypes = [vp, vp, u32, C.POINTER(KeyParams), vp, vp]
             L.rr_sort_workspace_size.argtypes = [u32, u32, u32, C.POINTER(C.c_size_t)]
             L.rr_sort.argtypes = [vp, vp, vp, u32, u32, u32, vp, C.c_size_t, vp]
+            L.rr_key_sort.argtypes = [vp, vp, u32, C.POINTER(KeyParams), vp, vp, u32, vp, C.c_size_t, vp]
             L.rr_sort_noalloc.argtypes = [vp, vp, vp, u32, u32, u32, vp]
             L.rr_permute.argtypes = [vp, vp, vp, vp, u32, vp, vp, vp, vp]
             L.rr_build_bvh.argtypes = [vp, u32, C.POINTER(vp)]
+            L.rr_bvh_serialize.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
+            L.rr_bvh_deserialize.argtypes = [vp, C.c_size_t, C.POINTER(vp)]
             L.rr_bvh_destroy.argtypes = [vp]
             L.rr_bvh_get_info.argtypes = [vp, C.POINTER(BvhInfo)]
             L.rr_trace.argtypes = [vp, vp, vp, u32, vp, vp]
@@ -152,6 +156,8 @@ def lib():
             L.rr_batch_run.argtypes = [vp, vp, vp, vp, vp, C.POINTER(BatchConfig), vp]
             L.rr_batch_run_loop.argtypes = [vp, vp, vp, vp, vp, C.POINTER(BatchConfig), vp]
             L.rr_batch_tune.argtypes = [vp, vp, vp, vp, C.POINTER(BatchConfig), C.POINTER(C.c_float), vp]
+            L.rr_batch_tune_cached.argtypes = [vp, vp, vp, vp, C.c_char_p, C.POINTER(BatchConfig),
+                                               C.POINTER(C.c_float), C.POINTER(C.c_uint32), vp]
             L.rr_server_create.argtypes = [C.POINTER(ServerConfig), C.POINTER(vp)]
             L.rr_server_add_scene.argtypes = [vp, vp, vp, C.POINTER(C.c_float), C.POINTER(C.c_float),
                                               C.POINTER(u32)]
@@ -248,6 +254,16 @@ def rr_sort(keys_in, keys_out, perm_out, n: int, bits: int, radix_bits: int, wor
                          _ptr(workspace), nbytes, _stream(stream)), "rr_sort")
 
 
+def rr_key_sort(o_tmin, d_tmax, params: KeyParams, keys_out, perm_out, radix_bits: int, workspace,
+                n: int | None = None, stream=None):
+    """rr_compute_keys followed by rr_sort of those keys, the sort's digit
+    counting done by the key kernel."""
+    n = o_tmin.shape[0] if n is None else n
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib().rr_key_sort(_ptr(o_tmin), _ptr(d_tmax), n, C.byref(params), _ptr(keys_out), _ptr(perm_out),
+                             radix_bits, _ptr(workspace), nbytes, _stream(stream)), "rr_key_sort")
+
+
 def rr_sort_segments(keys_in, keys_out, perm_out, n: int, bits: int, segment: int, stream=None):
     """Stable sort inside each run of `segment` consecutive keys (local sort)."""
     _check(lib().rr_sort_segments(_ptr(keys_in), _ptr(keys_out), _ptr(perm_out), n, bits, segment,
@@ -284,13 +300,28 @@ def rr_permute(o_tmin_in, d_tmax_in, payload_in, perm, o_tmin_out, d_tmax_out, p
 class BVH:
     """Owner of an rr_bvh handle built from a host triangle soup [T,9] float32."""
 
-    def __init__(self, tris: np.ndarray):
+    def __init__(self, tris: np.ndarray | None = None, *, serialized: bytes | None = None):
+        h = C.c_void_p()
+        if serialized is not None:
+            buf = C.create_string_buffer(bytes(serialized), len(serialized))
+            _check(lib().rr_bvh_deserialize(buf, len(serialized), C.byref(h)), "rr_bvh_deserialize")
+            self.handle = h.value
+            self.n_tris = self.info().n_tris
+            return
         tris = np.ascontiguousarray(tris, dtype=np.float32).reshape(-1, 9)
         self.n_tris = tris.shape[0]
-        h = C.c_void_p()
         _check(lib().rr_build_bvh(tris.ctypes.data if self.n_tris else None, self.n_tris,
                                   C.byref(h)), "rr_build_bvh")
         self.handle = h.value
+
+    def serialize(self) -> bytes:
+        """The BVH in rr_bvh_serialize's format (BVH(serialized=...) reloads it)."""
+        need = C.c_size_t()
+        _check(lib().rr_bvh_serialize(self.handle, None, C.byref(need)), "rr_bvh_serialize")
+        buf = C.create_string_buffer(need.value)
+        cap = C.c_size_t(need.value)
+        _check(lib().rr_bvh_serialize(self.handle, buf, C.byref(cap)), "rr_bvh_serialize")
+        return buf.raw[: cap.value]
 
     def info(self) -> BvhInfo:
         i = BvhInfo()
@@ -495,6 +526,16 @@ class Batch:
         _check(lib().rr_batch_tune(self.handle, _ptr(o_tmin), _ptr(d_tmax), _ptr(hits_out), C.byref(best),
                                    C.byref(ms), _stream(stream)), "rr_batch_tune")
         return best, float(ms.value)
+
+    def tune_cached(self, o_tmin, d_tmax, hits_out, cache_path: str, stream=None):
+        """rr_batch_tune_cached: (config, ms, from_cache)."""
+        best = BatchConfig()
+        ms = C.c_float()
+        hit = C.c_uint32()
+        _check(lib().rr_batch_tune_cached(self.handle, _ptr(o_tmin), _ptr(d_tmax), _ptr(hits_out),
+                                          os.fsencode(cache_path), C.byref(best), C.byref(ms), C.byref(hit),
+                                          _stream(stream)), "rr_batch_tune_cached")
+        return best, float(ms.value), bool(hit.value)
 
     def close(self):
         if getattr(self, "handle", None):

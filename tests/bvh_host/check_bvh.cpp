@@ -89,7 +89,135 @@ static void subtree_ids(Ctx &c, uint32_t ni, uint32_t depth, std::vector<uint32_
     }
 }
 
+// The serialized form: a round trip gives back the same arrays, box, depth and
+// leaf count; buffers damaged in each way the loader checks are refused.
+static bool refused(const std::vector<unsigned char> &buf) {
+    HostBVH back;
+    std::string err;
+    return deserialize_bvh(buf.data(), buf.size(), &back, &err) == RR_ERR_INVALID_ARG && !err.empty();
+}
+
+static void check_serialized(const HostBVH &h) {
+    std::vector<unsigned char> buf(serialized_bvh_bytes(h.nodes.size(), h.tris.size()));
+    serialize_bvh(h, buf.data());
+    HostBVH back;
+    std::string err;
+    if (deserialize_bvh(buf.data(), buf.size(), &back, &err) != RR_OK) {
+        fail_msg("round trip refused: " + err);
+        return;
+    }
+    if (back.nodes.size() != h.nodes.size() || back.tris.size() != h.tris.size() ||
+        back.planes.size() != h.planes.size() ||
+        std::memcmp(back.nodes.data(), h.nodes.data(), sizeof(RRNode8) * h.nodes.size()) ||
+        std::memcmp(back.tris.data(), h.tris.data(), sizeof(RRTri) * h.tris.size()) ||
+        std::memcmp(back.planes.data(), h.planes.data(), sizeof(float4) * h.planes.size()))
+        fail_msg("round trip changed the arrays");
+    if (back.depth != h.depth || back.stack_need != h.stack_need || back.n_leaves != h.n_leaves ||
+        std::memcmp(back.lo, h.lo, sizeof(h.lo)) || std::memcmp(back.hi, h.hi, sizeof(h.hi)))
+        fail_msg("round trip changed depth, leaf count or box");
+    auto node_at = [&](std::vector<unsigned char> &b, size_t i) {
+        return reinterpret_cast<RRNode8 *>(b.data() + kBvhHeaderBytes + sizeof(RRNode8) * i);
+    };
+    {
+        auto b = buf;
+        b[0] ^= 1u;
+        if (!refused(b)) fail_msg("bad magic accepted");
+    }
+    {
+        auto b = buf;
+        b.pop_back();
+        if (!refused(b)) fail_msg("truncated buffer accepted");
+    }
+    if (h.nodes.empty()) return;
+    {
+        auto b = buf;
+        node_at(b, 0)->tri_base = (uint32_t)h.tris.size();
+        if (node_at(b, 0)->tribits && !refused(b)) fail_msg("triangle range past the end accepted");
+    }
+    {
+        auto b = buf;
+        node_at(b, 0)->valid |= 1u << 9;
+        if (!refused(b)) fail_msg("slot mask above eight slots accepted");
+    }
+    {
+        auto b = buf;
+        const uint32_t bad = (uint32_t)h.tris.size();
+        std::memcpy(b.data() + kBvhHeaderBytes + sizeof(RRNode8) * h.nodes.size() + 12, &bad, 4);
+        if (!refused(b)) fail_msg("triangle id out of range accepted");
+    }
+    // a leaf slot of the root with malformed bits (two triangles, not the low ones)
+    for (int s = 0; s < 8; ++s) {
+        const RRNode8 &r = h.nodes[0];
+        if (((r.valid >> s) & 1u) && !((r.imask >> s) & 1u)) {
+            auto b = buf;
+            RRNode8 *nd = node_at(b, 0);
+            nd->tribits = (nd->tribits & ~(15u << (4 * s))) | (5u << (4 * s));
+            if (!refused(b)) fail_msg("malformed leaf bits accepted");
+            break;
+        }
+    }
+    if (h.nodes[0].imask) {
+        {
+            auto b = buf;
+            node_at(b, 0)->child_base = 0;  // the root as its own child: a cycle
+            if (!refused(b)) fail_msg("cycle accepted");
+        }
+        {
+            auto b = buf;
+            node_at(b, 0)->child_base = (uint32_t)h.nodes.size();
+            if (!refused(b)) fail_msg("child index past the end accepted");
+        }
+        {
+            auto b = buf;
+            node_at(b, 0)->imask |= (uint8_t)~h.nodes[0].valid;
+            if ((uint8_t)~h.nodes[0].valid && !refused(b)) fail_msg("inner child in an unused slot accepted");
+        }
+    }
+}
+
+// A chain of single-child nodes deeper than the trace kernel's stack, ending
+// in a one-triangle leaf: well formed in every other respect, refused for its
+// depth; one level shorter than the stack it loads.
+static void check_deep_chain() {
+    for (uint32_t levels : {kTraceStack, kTraceStack + 1}) {
+        HostBVH h;
+        h.nodes.resize(levels);
+        for (uint32_t i = 0; i < levels; ++i) {
+            RRNode8 &nd = h.nodes[i];
+            std::memset(&nd, 0, sizeof(nd));
+            nd.ex = nd.ey = nd.ez = 127;
+            nd.valid = 1u;
+            if (i + 1 < levels) {
+                nd.imask = 1u;
+                nd.child_base = i + 1;
+            } else {
+                nd.tribits = 1u;
+            }
+        }
+        h.tris.resize(1);
+        std::memset(h.tris.data(), 0, sizeof(RRTri));
+        h.planes.resize(2);
+        std::memset(h.planes.data(), 0, 2 * sizeof(float4));
+        for (int c = 0; c < 3; ++c) {
+            h.lo[c] = 0.0f;
+            h.hi[c] = 1.0f;
+        }
+        h.depth = levels;
+        h.n_leaves = 1;
+        std::vector<unsigned char> buf(serialized_bvh_bytes(h.nodes.size(), 1));
+        serialize_bvh(h, buf.data());
+        const bool ok = !refused(buf);
+        if (ok != (levels <= kTraceStack)) fail_msg("chain of " + std::to_string(levels) + " levels: wrong verdict");
+    }
+}
+
 int main(int argc, char **argv) {
+    if (argc >= 2 && std::string(argv[1]) == "--deep-chain") {
+        check_deep_chain();
+        if (fails) return 1;
+        std::printf("OK deep chain\n");
+        return 0;
+    }
     if (argc < 2) return 2;
     std::vector<float> tris;
     if (FILE *f = std::fopen(argv[1], "rb")) {
@@ -142,6 +270,7 @@ int main(int argc, char **argv) {
                 }
         }
     }
+    check_serialized(h);
     if (fails) return 1;
     std::printf("OK n=%u nodes=%zu leaves=%u depth=%u\n", n, h.nodes.size(), h.n_leaves, h.depth);
     return 0;

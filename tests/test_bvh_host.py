@@ -6,7 +6,8 @@ exactly one leaf, that each slot's quantised box (decoded from the node's frame
 and exponents) contains every vertex under it with at least one quantisation
 step to spare, that child and triangle indices and leaf bits are well formed,
 that the depth fits the trace kernel's stack, and that the stored plane normals
-are the binary64 cross products.
+are the binary64 cross products, and that the serialized form round-trips
+and refuses damaged buffers.
 """
 import os
 import shutil
@@ -60,3 +61,10 @@ def _soups():
 def test_bvh_invariants(checker, tmp_path, name):
     out = _run(checker, _soups()[name], tmp_path)
     assert out.startswith("OK")
+
+
+def test_serialized_bvh_rejects_too_deep_chain(checker):
+    """A chain of single-child nodes one level deeper than the trace kernel's
+    stack is refused by the loader; one as deep as the stack is accepted."""
+    r = subprocess.run([checker, "--deep-chain"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr

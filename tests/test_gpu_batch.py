@@ -285,3 +285,45 @@ def test_batch_config_layout_overrides_the_key(world):
     assert best.layout in (-1, rr.RR_KEY_COSTA, rr.RR_KEY_AILA_COMPACT)
     assert rr.rr_device_error() == 0
     b.close()
+
+
+def test_batch_tune_cached(world, tmp_path):
+    """The first call tunes and writes the file; a second batch of the same
+    kind takes the entry without timing; a batch of another size bucket is
+    tuned again and its entry added; the file is JSON any reader can parse."""
+    import json
+    import time
+    path = str(tmp_path / "tune.json")
+    o, d = _dev(world["o"]), _dev(world["d"])
+    b = make_batch(world, rr.RR_KEY_AILA)
+    h = torch.empty(b.n, 4, device="cuda")
+    best, ms, hit = b.tune_cached(o, d, h, path)
+    assert not hit and ms > 0 and best.radix_bits in (4, 8) and best.trace_block in (128, 256, 512)
+    doc = json.load(open(path))
+    assert doc["format"] == "rr-batch-tune-cache" and len(doc["entries"]) == 1
+    (key, entry), = doc["entries"].items()
+    assert "rays2^" in key and entry["key_bits"] == best.key_bits and entry["trace_block"] == best.trace_block
+    b2 = make_batch(world, rr.RR_KEY_AILA)
+    t0 = time.perf_counter()
+    best2, ms2, hit2 = b2.tune_cached(o, d, h, path)
+    dt = time.perf_counter() - t0
+    assert hit2 and dt < 0.05
+    assert (best2.key_bits, best2.radix_bits, best2.trace_block, best2.layout) == \
+        (best.key_bits, best.radix_bits, best.trace_block, best.layout)
+    assert abs(ms2 - ms) <= 1e-3 * ms
+    b2.run(o, d, h, best2)  # the cached configuration runs
+    # another layout is another entry
+    b3 = make_batch(world, rr.RR_KEY_COSTA)
+    _, _, hit3 = b3.tune_cached(o, d, h, path)
+    assert not hit3 and len(json.load(open(path))["entries"]) == 2
+    # an entry the batch cannot run is tuned again and replaced
+    doc = json.load(open(path))
+    doc["entries"][key]["radix_bits"] = 5
+    json.dump(doc, open(path, "w"))
+    _, _, hit4 = b.tune_cached(o, d, h, path)
+    assert not hit4 and json.load(open(path))["entries"][key]["radix_bits"] in (4, 8)
+    with pytest.raises(rr.RRError):
+        b.tune_cached(o, d, h, str(tmp_path / "no_such_dir" / "tune.json"))
+    for x in (b, b2, b3):
+        x.close()
+    assert rr.rr_device_error() == 0
