@@ -904,7 +904,7 @@ def bench_serving(args, dev, slots: int = 4, max_batch_rays: int = 1 << 23, frac
     lo_n, hi_n = int(4096 * scale) + 1, int(SERVE_MAX_REQ * scale)
     pool_n = max(1024, int(SERVE_POOL * scale))
     srv = rr.Server(budget_bytes=SERVE_BUDGET, slots=slots, max_batch_rays=max(max_batch_rays, hi_n), key_bits=24,
-                    radix_bits=8, trace_block=256, reserve_bytes=reserve)
+                    radix_bits=8, trace_block=128, reserve_bytes=reserve)
     scenes = []
     pools = {}
     t0 = time.time()

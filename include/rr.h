@@ -580,7 +580,8 @@ typedef struct {
     float ratio;               /* FIXED estimate ratio */
     uint32_t key_bits;         /* bits of each request's own key (capped at 64 - request bits) */
     uint32_t radix_bits;       /* 4 or 8 */
-    uint32_t trace_block;      /* 128, 256 or 512 */
+    uint32_t trace_block;      /* 128, 256 or 512; 128 lets the host-link copy kernel of RR_UPLOAD_KERNEL
+                                  run beside a full trace (one warp per SM fits in its registers) */
     uint64_t reserve_bytes;    /* device memory taken from the pool and returned at creation, so
                                   that the first groups do not wait for the pool to grow (0: none;
                                   at most budget_bytes) */

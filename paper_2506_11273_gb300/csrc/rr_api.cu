@@ -234,14 +234,18 @@ void *mapped_host_range(const void *host, size_t bytes) {
 }
 
 namespace {
-// Eight 16-byte words per thread per round, strided over the grid: one block
-// per SM keeps 32 KB of host-link reads in flight, enough for the link's
-// rate while taking few warp slots from kernels running beside it.
-constexpr int kCopyDepth = 8;
-__global__ void __launch_bounds__(256) kernel_copy_kernel(const uint4 *__restrict__ src, uint4 *__restrict__ dst,
-                                                         size_t n16) {
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per block, four 16-byte words per thread per round, strided over
+// the grid.  A one-warp block at no more than 32 registers fits beside a
+// persistent trace kernel that fills an SM (nine 128-thread blocks at 56
+// registers leave 1,024 registers), so a copy for the next group runs while
+// the current group's trace does instead of waiting for it to drain; one such
+// warp per SM keeps ~300 KB of host-link reads in flight.
+constexpr int kCopyDepth = 4;
+constexpr int kCopyWarp = 32;
+__global__ void __maxnreg__(32) kernel_copy_kernel(const uint4 *__restrict__ src,
+                                                   uint4 *__restrict__ dst, size_t n16) {
+    const size_t stride = (size_t)gridDim.x * kCopyWarp;
+    size_t i = (size_t)blockIdx.x * kCopyWarp + threadIdx.x;
     for (; i + (kCopyDepth - 1) * stride < n16; i += kCopyDepth * stride) {
         uint4 v[kCopyDepth];
 #pragma unroll
@@ -256,9 +260,9 @@ __global__ void __launch_bounds__(256) kernel_copy_kernel(const uint4 *__restric
 rr_status enqueue_kernel_copy(void *dst, const void *src, size_t bytes, int sm_count, cudaStream_t s) {
     if (bytes == 0) return RR_OK;
     const size_t n16 = bytes / 16;
-    const size_t want = (n16 + 256 * kCopyDepth - 1) / (256 * kCopyDepth);  // blocks that each get a full round
+    const size_t want = (n16 + kCopyWarp * kCopyDepth - 1) / (kCopyWarp * kCopyDepth);  // blocks with a full round
     const uint32_t blocks = (uint32_t)std::max<size_t>(1, std::min<size_t>(want, (size_t)sm_count));
-    kernel_copy_kernel<<<blocks, 256, 0, s>>>(static_cast<const uint4 *>(src), static_cast<uint4 *>(dst), n16);
+    kernel_copy_kernel<<<blocks, kCopyWarp, 0, s>>>(static_cast<const uint4 *>(src), static_cast<uint4 *>(dst), n16);
     note_launches(1);
     return check_launch("host-link copy");
 }

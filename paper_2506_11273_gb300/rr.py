@@ -559,7 +559,7 @@ class Server:
 
     def __init__(self, budget_bytes: int, slots: int = 4, max_batch_rays: int = 1 << 24,
                  layout: int = RR_KEY_TWO_POINT, t_source: int = RR_T_FIXED, ratio: float = 0.25,
-                 key_bits: int = 24, radix_bits: int = 8, trace_block: int = 256, reserve_bytes: int = 0,
+                 key_bits: int = 24, radix_bits: int = 8, trace_block: int = 128, reserve_bytes: int = 0,
                  upload: int = 0):
         cfg = ServerConfig(int(budget_bytes), slots, max_batch_rays, layout, t_source, float(np.float32(ratio)),
                            key_bits, radix_bits, trace_block, int(reserve_bytes), int(upload))
