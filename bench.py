@@ -45,11 +45,11 @@ BYTES_ACCUM = 32 + 16
 TRACE_SOURCES = ["paper_2506_11273_gb300/csrc/rr_trace.cu", "paper_2506_11273_gb300/csrc/rr_trace.h",
                  "paper_2506_11273_gb300/csrc/rr_common.cuh", "paper_2506_11273_gb300/csrc/rr_bvh.cpp",
                  "paper_2506_11273_gb300/csrc/rr_keymath.cuh", "paper_2506_11273_gb300/csrc/rr_batch.cuh"]
-# One ncu capture of the fused trace kernel on this workload (bounce-3 wavefront,
-# sorted rays): DRAM bytes read + written and warp instructions per launch, valid
-# only while the trace sources hash to `sources` (sha256 of TRACE_SOURCES, first
-# 16 hex digits); otherwise traffic is reported as null.
-TRACE_NCU = {"sources": "84306fa47ac172e5", "dram_bytes": 171198208 + 16528128, "warp_instructions": 540315360}
+# One ncu capture of the trace kernel on this workload (bounce-3 wavefront, sorted
+# rays, `trace_kernel<0, 0, 0, 128>`): DRAM bytes read + written and warp
+# instructions per launch, valid only while the trace sources hash to `sources`
+# (sha256 of TRACE_SOURCES, first 16 hex digits); otherwise traffic is reported as null.
+TRACE_NCU = {"sources": "16c2fbc1e738e3cd", "dram_bytes": 171183616 + 16250624, "warp_instructions": 540485561}
 # issue-slot peak: 4 warp instructions per cycle per SM (one per scheduler) x 152 SMs
 SMS, ISSUE_PER_SM_CYCLE, MAX_SM_MHZ = 152, 4, 2070.0
 
