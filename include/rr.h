@@ -397,14 +397,9 @@ rr_status rr_pipeline_run(rr_pipeline *p, const float *o_tmin, const float *d_tm
  * rr_pipeline_submit_host - one bounce on host buffers, enqueued without
  * waiting.  Submissions alternate between two device staging slots, so the
  * upload of one submission overlaps the kernels of the one before: rays and
- * payloads go up on the handle's upload stream, the bounce runs on `stream`,
- * sorted payloads come back on the handle's side stream while the trace runs.
- * When hits_host is page-locked host memory (cudaHostAlloc or
- * cudaHostRegister) over its whole n * 16 bytes and 16-byte aligned, the trace
- * kernel stores the hits there directly, so their transfer overlaps the trace;
- * otherwise they are staged on the device and copied back after it.  Both
- * forms give the same bytes.  A hits_host whose first and last bytes are
- * page-locked must be page-locked in between (one allocation).
+ * payloads go up on the handle's upload stream, the bounce runs on `stream`
+ * with its hits staged in the slot, and the sorted payloads and the hits come
+ * back on the handle's side stream while the next submission computes.
  *
  * *ticket receives a number for rr_pipeline_wait (0 for n == 0).  Until that
  * wait returns, the host buffers of the submission must stay allocated, its

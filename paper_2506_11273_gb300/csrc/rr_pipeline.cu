@@ -8,11 +8,12 @@
 struct HostSlot {
     float *o_in = nullptr, *d_in = nullptr;  // uploaded rays
     uint32_t *payload_in = nullptr, *payload_sorted = nullptr;
-    float *hits = nullptr;  // hits staged here when the caller's buffer is pageable
+    float *hits = nullptr;  // hits staged here, then copied back on the side stream
     cudaEvent_t rays_up = nullptr, pay_up = nullptr;  // upload stream: rays, payloads arrived
     cudaEvent_t consumed = nullptr;  // main stream: the reorder has read this slot's inputs
+    cudaEvent_t traced = nullptr;    // main stream: the trace has written this slot's hits
     cudaEvent_t pay_down = nullptr;  // side stream: sorted payloads returned
-    cudaEvent_t done = nullptr;      // main stream: hits written (and returned)
+    cudaEvent_t done = nullptr;      // side stream: hits returned (the slot's hits buffer is free)
 };
 
 struct rr_pipeline {
@@ -33,24 +34,6 @@ struct rr_pipeline {
 
 namespace {
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-// Device address of `bytes` of page-locked host memory at `host`, or null when
-// either end of the range is not page-locked, mapped host memory (pageable
-// memory takes the copy path).  Kernels then store into it directly over the
-// host link.
-void *mapped_host(void *host, size_t bytes) {
-    cudaPointerAttributes a{}, b{};
-    if (cudaPointerGetAttributes(&a, host) != cudaSuccess ||
-        cudaPointerGetAttributes(&b, static_cast<char *>(host) + bytes - 1) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
-        return nullptr;
-    if (static_cast<char *>(b.devicePointer) - static_cast<char *>(a.devicePointer) != (ptrdiff_t)(bytes - 1))
-        return nullptr;
-    return a.devicePointer;
-}
 }  // namespace
 
 using namespace rr;
@@ -110,7 +93,7 @@ extern "C" rr_status rr_pipeline_create(const rr_bvh *bvh, uint32_t max_n, const
     e = cudaStreamCreateWithFlags(&p->upload, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
     for (HostSlot &h : p->slot)
-        for (cudaEvent_t *ev : {&h.rays_up, &h.pay_up, &h.consumed, &h.pay_down, &h.done})
+        for (cudaEvent_t *ev : {&h.rays_up, &h.pay_up, &h.consumed, &h.traced, &h.pay_down, &h.done})
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         rr_pipeline_destroy(p);
@@ -123,10 +106,10 @@ extern "C" rr_status rr_pipeline_create(const rr_bvh *bvh, uint32_t max_n, const
 extern "C" rr_status rr_pipeline_destroy(rr_pipeline *p) {
     if (!p) return RR_OK;
     for (HostSlot &h : p->slot)
-        for (cudaEvent_t ev : {h.rays_up, h.pay_up, h.consumed, h.pay_down, h.done})
+        for (cudaEvent_t ev : {h.rays_up, h.pay_up, h.consumed, h.traced, h.pay_down, h.done})
             if (ev) cudaEventSynchronize(ev);
     for (HostSlot &h : p->slot)
-        for (cudaEvent_t ev : {h.rays_up, h.pay_up, h.consumed, h.pay_down, h.done})
+        for (cudaEvent_t ev : {h.rays_up, h.pay_up, h.consumed, h.traced, h.pay_down, h.done})
             if (ev) cudaEventDestroy(ev);
     if (p->upload) cudaStreamDestroy(p->upload);
     if (p->side) cudaStreamDestroy(p->side);
@@ -144,6 +127,7 @@ struct BounceSync {
     cudaEvent_t payload_ready = nullptr; // wait before the reorder
     cudaEvent_t payload_free = nullptr;  // wait before the reorder (previous reader of payload_out)
     cudaEvent_t consumed = nullptr;      // record after the reorder
+    cudaEvent_t hits_free = nullptr;     // wait before the trace (previous reader of hits_out)
 };
 
 rr_status wait_on(cudaStream_t s, cudaEvent_t ev) {
@@ -169,6 +153,8 @@ rr_status run_bounce(rr_pipeline *p, const float *o_tmin, const float *d_tmax, c
         const cudaError_t e = cudaEventRecord(sync.consumed, s);
         if (e != cudaSuccess) return fail_cuda(e, "rr_pipeline: record");
     }
+    st = wait_on(s, sync.hits_free);
+    if (st != RR_OK) return st;
     if (p->params.layout == RR_KEY_TWO_POINT && p->params.t_source == RR_T_ADAPTIVE)
         return rr_trace_accumulate(p->bvh, p->o_sorted, p->d_sorted, n, hits_out,
                                    const_cast<rr_length_table *>(p->params.table), stream);
@@ -190,10 +176,10 @@ extern "C" rr_status rr_pipeline_run(rr_pipeline *p, const float *o_tmin, const 
 
 // Host buffers, without waiting.  Submission k uses staging slot k mod 2: its
 // rays and payloads go up on the upload stream (after submission k-2 has
-// read the slot), the bounce runs on `stream`, the sorted payloads come back
-// on the side stream while the trace runs, and hits in page-locked host
-// memory are stored there by the trace kernel itself (otherwise staged on the
-// device and copied back on `stream` after it).
+// read the slot), the bounce runs on `stream` with the hits staged in the
+// slot (after submission k-2's hits have gone back), and the sorted payloads
+// and the hits come back on the side stream while the next submission
+// computes.
 extern "C" rr_status rr_pipeline_submit_host(rr_pipeline *p, const float *o_host, const float *d_host,
                                              const uint32_t *payload_host, uint32_t n, float *hits_host,
                                              uint32_t *payload_out_host, void *stream, uint64_t *ticket) {
@@ -208,8 +194,6 @@ extern "C" rr_status rr_pipeline_submit_host(rr_pipeline *p, const float *o_host
     const uint64_t k = p->submitted++;
     HostSlot &h = p->slot[k & 1];
     const bool pay = payload_host != nullptr;
-    float *hits_direct = static_cast<float *>(mapped_host(hits_host, 16ull * n));
-    if (hits_direct && !aligned(hits_direct, 16)) hits_direct = nullptr;
     // uploads: after the reorder of submission k-2 has read this slot
     cudaError_t e = cudaStreamWaitEvent(p->upload, h.consumed, 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h.o_in, o_host, 16ull * n, cudaMemcpyHostToDevice, p->upload);
@@ -226,7 +210,8 @@ extern "C" rr_status rr_pipeline_submit_host(rr_pipeline *p, const float *o_host
     sync.payload_ready = pay ? h.pay_up : nullptr;
     sync.payload_free = pay ? h.pay_down : nullptr;
     sync.consumed = h.consumed;
-    rr_status st = run_bounce(p, h.o_in, h.d_in, pay ? h.payload_in : nullptr, n, hits_direct ? hits_direct : h.hits,
+    sync.hits_free = h.done;
+    rr_status st = run_bounce(p, h.o_in, h.d_in, pay ? h.payload_in : nullptr, n, h.hits,
                               pay ? h.payload_sorted : nullptr, stream, sync);
     if (st != RR_OK) return st;
     if (pay) {
@@ -237,8 +222,11 @@ extern "C" rr_status rr_pipeline_submit_host(rr_pipeline *p, const float *o_host
     // recorded for every submission, so that it also covers the payload
     // downloads of earlier submissions still running on the side stream
     if (e == cudaSuccess) e = cudaEventRecord(h.pay_down, p->side);
-    if (e == cudaSuccess && !hits_direct) e = cudaMemcpyAsync(hits_host, h.hits, 16ull * n, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaEventRecord(h.done, s);
+    // the hits come back on the side stream while the next submission computes
+    if (e == cudaSuccess) e = cudaEventRecord(h.traced, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, h.traced, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hits_host, h.hits, 16ull * n, cudaMemcpyDeviceToHost, p->side);
+    if (e == cudaSuccess) e = cudaEventRecord(h.done, p->side);
     if (e != cudaSuccess) return fail_cuda(e, "rr_pipeline_submit_host: download");
     if (ticket) *ticket = k + 1;
     return RR_OK;
@@ -250,9 +238,9 @@ extern "C" rr_status rr_pipeline_wait(rr_pipeline *p, uint64_t ticket) {
     if (ticket > p->submitted) return fail(RR_ERR_INVALID_ARG, "rr_pipeline_wait: ticket was never issued");
     if (fault_fires(Fault::Timeout)) return fail(RR_ERR_TIMEOUT, "rr_pipeline_wait: injected time-out");
     // a slot's events are re-recorded by later submissions; those complete
-    // after this one, so waiting on them is never too early.  `done` follows
-    // every earlier submission on the caller's stream and `pay_down` every
-    // earlier payload download on the side stream.
+    // after this one, so waiting on them is never too early.  `done` and
+    // `pay_down` follow every earlier download on the side stream, and each
+    // hit download follows its own submission's trace.
     HostSlot &h = p->slot[(ticket - 1) & 1];
     cudaError_t e = cudaEventSynchronize(h.done);
     if (e == cudaSuccess) e = cudaEventSynchronize(h.pay_down);

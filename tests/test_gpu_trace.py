@@ -242,9 +242,8 @@ def test_pipeline_matches_oracle_config1(name, layout, olayout, bits, tsrc, otsr
     hits = torch.empty(len(rays), 4, device="cuda")
     pout = torch.empty_like(p)
     n = len(rays)
-    # host entries: pageable buffers (copies), page-locked buffers (the trace
-    # stores hits straight into host memory), page-locked hits at an offset
-    # inside their allocation with pageable payloads (mixed)
+    # host entries: pageable buffers, page-locked buffers, page-locked hits at
+    # an offset inside their allocation with pageable payloads (mixed)
     for entry in ("device", "host", "host_pinned", "host_mixed"):
         if adaptive:
             table.reset()
