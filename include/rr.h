@@ -21,9 +21,11 @@
  *                        fused into the key kernel
  *   rr_sort_segments     local (block-wise) sort (Section 3.2)
  *   rr_coherence_capsule the capsule coherence measure (Section 4.3)
+ *   rr_bvh_serialize, rr_bvh_deserialize
+ *                        store a built BVH and reload it (checked before upload)
  *   rr_pipeline_*        one bounce behind one handle
  *   rr_batch_*           many wavefronts over resident scenes as one CUDA graph, with
- *                        an autotuner
+ *                        an autotuner and its JSON cache
  *   rr_server_*          a serving loop with continuous batching under a memory budget
  *
  * Conventions shared by every call:
