@@ -86,6 +86,20 @@ def test_key_sort_adaptive_table(soup):
     tab.close()
 
 
+def test_key_sort_given_estimate(soup):
+    """GIVEN estimates (the oracle's hit distances; misses are +inf, which the
+    key replaces by 4E) through the fused call."""
+    tris, rays, lo, hi = soup
+    hits, _ = oracle.BVH(tris).trace(rays.o_tmin, rays.d_tmax)
+    t = np.ascontiguousarray(hits[:, 0], np.float32)
+    tg = torch.from_numpy(t).cuda()
+    for bits, radix_bits in ((64, 8), (48, 4), (20, 8)):
+        p = rr.key_params(rr.RR_KEY_TWO_POINT, bits, lo, hi, t_source=rr.RR_T_GIVEN, t_given=tg)
+        k_gpu, perm_gpu = key_sort(rays, p, radix_bits)
+        k_or, perm_or = oracle_key_sort(rays, oracle.TWO_POINT, bits, lo, hi, tsrc=oracle.T_GIVEN, t_given=t)
+        assert np.array_equal(k_gpu, k_or) and np.array_equal(perm_gpu, perm_or), (bits, radix_bits)
+
+
 def test_key_sort_long_passes_and_workspace_reuse():
     """Enough rays for every key block to loop over several tiles and for the
     digit passes to take the four-blocks-per-SM form (at least eight 3072-key
