@@ -2,7 +2,8 @@
 
 * Path tracer (1,168,576 triangles), a 1,196,335-ray wavefront (the bounce-3
   size) through the timed step: Two Point key with the adaptive estimate at 64
-  bits, 8-bit radix sort, gather, trace with the fused length-table update.
+  bits and its 8-bit radix sort in one rr_key_sort call, gather, trace, then
+  the length-table update.
   Every key, the whole permutation and every reordered ray are compared; hits
   on a 20,000-ray sample; the table after the update against the oracle's.
 * Batched: 32 wavefronts (17,808,070 rays) over 4 resident scenes as one graph
@@ -54,8 +55,14 @@ def test_path_tracer_step_full_size():
     so, sd, sp = torch.empty_like(o), torch.empty_like(d), torch.empty_like(p)
     hits = torch.empty(n, 4, device="cuda")
     params = rr.key_params(rr.RR_KEY_TWO_POINT, 64, lo, hi, t_source=rr.RR_T_ADAPTIVE, table=table)
-    rr.rr_compute_keys(o, d, params, keys)
-    rr.rr_sort(keys, None, perm, n, 64, 8, rr.sort_workspace(n, 64, 8))
+    ws = rr.sort_workspace(n, 64, 8)
+    rr.rr_key_sort(o, d, params, keys, perm, 8, ws)
+    # the two-call form (keys, then the sort with its own counting pass), on
+    # the same table before the trace updates it
+    keys2 = torch.empty_like(keys)
+    perm2 = torch.empty_like(perm)
+    rr.rr_compute_keys(o, d, params, keys2)
+    rr.rr_sort(keys2, None, perm2, n, 64, 8, rr.sort_workspace(n, 64, 8))
     rr.rr_permute(o, d, p, perm, so, sd, sp)
     rr.rr_trace_accumulate(bvh, so, sd, hits, table)
     k_or = oracle.compute_keys(oracle.TWO_POINT, 64, rays.o_tmin, rays.d_tmax, lo, hi, tsrc=oracle.T_ADAPTIVE,
@@ -63,6 +70,7 @@ def test_path_tracer_step_full_size():
     assert np.array_equal(rr.keys_to_numpy(keys), k_or)
     p_or, _ = oracle.stable_sort(k_or)
     assert np.array_equal(rr.u32_to_numpy(perm), p_or)
+    assert torch.equal(keys2, keys) and torch.equal(perm2, perm)
     oo, od, op = oracle.permute(rays.o_tmin, rays.d_tmax, rays.payload, p_or)
     assert np.array_equal(_bits(so.cpu().numpy()), _bits(oo))
     assert np.array_equal(_bits(sd.cpu().numpy()), _bits(od))
