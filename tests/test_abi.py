@@ -98,3 +98,33 @@ def test_host_argument_checks_without_a_gpu(librr):
         h = ctypes.c_void_p()
         assert lib.rr_build_bvh(tri, 1, ctypes.byref(h)) == 2  # RR_ERR_CUDA: no device, no crash
         assert not h.value
+
+
+def test_header_is_plain_c_and_links(librr, tmp_path):
+    """include/rr.h compiles as C11 and as C++17, and a C program built
+    against it links with librr.so and calls a host-only entry point."""
+    import shutil
+    if shutil.which("gcc") is None or shutil.which("g++") is None:
+        pytest.skip("gcc/g++ missing")
+    inc = os.path.dirname(HEADER)
+    for cc, std, lang in (("gcc", "-std=c11", "c"), ("g++", "-std=c++17", "c++")):
+        r = subprocess.run([cc, "-fsyntax-only", std, "-Wall", "-Wextra", "-Werror", "-x", lang, HEADER],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+    src = tmp_path / "use_rr.c"
+    src.write_text('#include <stdio.h>\n#include <string.h>\n#include "rr.h"\n'
+                   'int main(void) {\n'
+                   '    const char *s = rr_status_string(RR_ERR_INVALID_ARG);\n'
+                   '    if (!s || strcmp(s, "invalid argument") != 0) return 1;\n'
+                   '    size_t b = 0;\n'
+                   '    if (rr_sort_workspace_size(1000, 64, 8, &b) != RR_OK || b == 0) return 2;\n'
+                   '    if (rr_sort_workspace_size(1000, 65, 8, &b) != RR_ERR_INVALID_ARG) return 3;\n'
+                   '    puts("ok");\n'
+                   '    return 0;\n'
+                   '}\n')
+    exe = tmp_path / "use_rr"
+    r = subprocess.run(["gcc", "-std=c11", "-I", inc, str(src), librr, "-Wl,-rpath," + os.path.dirname(librr),
+                        "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
