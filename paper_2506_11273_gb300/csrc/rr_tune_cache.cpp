@@ -5,6 +5,7 @@
 
 #include <unistd.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -227,7 +228,10 @@ bool tune_cache_store(const std::string &path, const std::string &key, const Tun
         first = false;
     }
     o << "\n}}\n";
-    const std::string tmp = path + ".tmp." + std::to_string((long)getpid());
+    // a name of its own per process and call, so that concurrent writers
+    // never share a temporary file
+    static std::atomic<uint64_t> serial{0};
+    const std::string tmp = path + ".tmp." + std::to_string((long)getpid()) + "." + std::to_string(serial++);
     {
         std::ofstream f(tmp, std::ios::binary | std::ios::trunc);
         if (!f) {

@@ -90,3 +90,20 @@ def test_unwritable_path_reports_failure(cli, tmp_path):
     f = tmp_path / "missing_dir" / "tune.json"
     out = run(cli, f, "store", KEY, 24, 8, 128, -1, 1.0)
     assert out.startswith("FAIL") and "cannot write" in out
+
+
+def test_concurrent_writers_keep_a_valid_file(cli, tmp_path):
+    """Eight processes storing different keys at once: the file is always whole
+    JSON (each writer renames its own temporary file over it) and holds at
+    least the last writer's entry; no temporary file is left."""
+    f = tmp_path / "tune.json"
+    procs = [subprocess.Popen([cli, str(f), "store", "k%d" % i] + [str(x) for x in (8 + i, 8, 128, -1, 1.0 + i)],
+                              stdout=subprocess.PIPE, text=True) for i in range(8)]
+    outs = [p.communicate()[0].strip() for p in procs]
+    assert outs == ["OK"] * 8
+    doc = json.loads(f.read_text())
+    assert doc["format"] == "rr-batch-tune-cache" and len(doc["entries"]) >= 1
+    for k, e in doc["entries"].items():
+        i = int(k[1:])
+        assert e == {"key_bits": 8 + i, "radix_bits": 8, "trace_block": 128, "layout": -1, "ms": 1.0 + i}
+    assert not [p for p in os.listdir(tmp_path) if ".tmp." in p]
