@@ -125,11 +125,19 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index: int):
+    def __init__(self, device_index: int, window: str = "the timed region"):
         self.dev = device_index
+        self.window = window
         self.p = None
         self.out = None
-        self.path = "/tmp/rr_clocks_%d.csv" % os.getpid()
+        self.skip = 0
+        self.path = "/tmp/rr_clocks_%d_%d.csv" % (os.getpid(), device_index)
+
+    def _lines(self) -> int:
+        try:
+            return open(self.path).read().count("\n")
+        except OSError:
+            return 0
 
     def __enter__(self):
         try:
@@ -139,6 +147,13 @@ class ClockSampler:
                                       stdout=self.out, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.p = None
+        if self.p is not None:
+            # the sampler is live before the window opens; its samples from
+            # before the window are left out of the summary
+            t_end = time.time() + 3.0
+            while self._lines() == 0 and time.time() < t_end and self.p.poll() is None:
+                time.sleep(0.02)
+            self.skip = self._lines()
         return self
 
     def __exit__(self, *a):
@@ -157,8 +172,10 @@ class ClockSampler:
             os.remove(self.path)
         except OSError:
             rows = []
+        inside = rows[self.skip:]
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "window": self.window}
+        rows = inside or rows[-1:]
         sm = [float(r[1]) for r in rows if len(r) > 8]
         mx = [float(r[2]) for r in rows if len(r) > 8]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -169,7 +186,8 @@ class ClockSampler:
                     if r[5 + k].strip().lower() == "active":
                         reasons.add(name)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "samples_in_window": len(inside),
+                "window": self.window}
 
 
 def build_workload(small: bool, seed: int):
@@ -316,13 +334,21 @@ def run_ours(args):
     n = B["n"]
     step_tp, phases_tp = make_step(B, params_tp, True, sort="fused")
     l0 = rr.rr_kernel_launch_count()
-    with ClockSampler(local) as clk:
-        total_ms, times, ph = timed(step_tp, args.steps, args.warmup, phases_tp)
-    launches = (rr.rr_kernel_launch_count() - l0)
-    launches_timed = launches * args.steps // (args.steps + args.warmup)
-    # the same step with keys and sort as two calls: the key and sort phases
-    # on their own (for their HBM fractions)
     step_sep, phases_sep = make_step(B, params_tp, True)
+    # clocks: nvidia-smi samples every 100 ms, longer than the timed steps, so
+    # the window also covers the same step run untimed for 0.4 s right after
+    # them, under the same load
+    with ClockSampler(local, "the timed steps and 0.4 s of the same step right after them") as clk:
+        total_ms, times, ph = timed(step_tp, args.steps, args.warmup, phases_tp)
+        launches = (rr.rr_kernel_launch_count() - l0)
+        launches_timed = launches * args.steps // (args.steps + args.warmup)
+        t_soak = time.time()
+        while time.time() - t_soak < 0.4:
+            flush.zero_()
+            step_tp()
+            torch.cuda.synchronize()
+    # the same step with keys and sort as two calls: the key and sort phases on
+    # their own (for their HBM fractions)
     _, _, ph_sep = timed(step_sep, max(3, args.steps // 2), 3, phases_sep)
     E_scene = float(np.max(hi - lo))
 
